@@ -1,0 +1,293 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things fixed outside itself: exact integer
+predicates, an O(n^3) brute-force hull and Andrew's monotone chain written
+from the definition of the result (tests/exact_ref.py), closed forms, the
+paper's byte-model totals (Sec. 5.2) and invariance under exact transforms.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import exact_ref as E
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(autouse=True)
+def _filter_on():
+    oracle.set_filter(True)
+    yield
+    oracle.set_filter(True)
+
+
+def _near_degenerate_triples(rng, count):
+    """Shewchuk-style grids: c near the line a->b, perturbed by a few ulps."""
+    out = []
+    for _ in range(count):
+        kind = rng.integers(0, 4)
+        if kind == 0:
+            a = (0.5, 0.5)
+            b = (12.0, 12.0)
+            base = 24.0
+            i, j = rng.integers(-8, 9, 2)
+            c = (base + i * math.ulp(base), base + j * math.ulp(base))
+        elif kind == 1:
+            t = rng.random(3)
+            a = (t[0], 2 * t[0])
+            b = (t[1], 2 * t[1])
+            c = (t[2], np.nextafter(2 * t[2], np.inf if rng.random() < 0.5 else -np.inf))
+        elif kind == 2:
+            s = 2.0 ** rng.integers(-300, 300)
+            a = tuple(s * rng.random(2))
+            b = tuple(s * rng.random(2))
+            w = rng.random()
+            c = (a[0] + w * (b[0] - a[0]), a[1] + w * (b[1] - a[1]))
+        else:
+            a = tuple(rng.integers(-3, 4, 2).astype(float))
+            b = tuple(rng.integers(-3, 4, 2).astype(float))
+            c = tuple(rng.integers(-3, 4, 2).astype(float))
+        out.append((a, b, c))
+    return out
+
+
+@pytest.mark.parametrize("use_filter", [True, False])
+def test_orient_sign_matches_integer_arithmetic(use_filter):
+    oracle.set_filter(use_filter)
+    rng = np.random.default_rng(11)
+    before = oracle._load().orc_exact_count()
+    zeros = 0
+    for a, b, c in _near_degenerate_triples(rng, 3000):
+        got = oracle.orient_sign(a, b, c)
+        want = E.orient_sign_exact(a, b, c)
+        assert got == want, (a, b, c, got, want)
+        zeros += want == 0
+    assert zeros > 50  # exact collinear cases were exercised
+    assert oracle._load().orc_exact_count() > before  # and the exact path ran
+
+
+@pytest.mark.parametrize("use_filter", [True, False])
+def test_cross_and_dot_signs(use_filter):
+    oracle.set_filter(use_filter)
+    rng = np.random.default_rng(12)
+    for _ in range(2000):
+        if rng.random() < 0.5:
+            pts = [tuple(rng.integers(-4, 5, 2).astype(float)) for _ in range(4)]
+        else:
+            base = rng.random(2)
+            d = rng.random(2)
+            pts = [tuple(base), tuple(base + d)]
+            k = rng.random()
+            q0 = base + rng.random() * d
+            q1 = q0 + k * d
+            q1 = (q1[0], np.nextafter(q1[1], np.inf) if rng.random() < 0.5 else q1[1])
+            pts += [tuple(q0), tuple(q1)]
+        assert oracle.cross_sign(*pts) == E.cross_sign_exact(*pts), pts
+        assert oracle.dot_sign(*pts) == E.dot_sign_exact(*pts), pts
+
+
+def _tiny_sets(rng, count):
+    for t in range(count):
+        n = int(rng.integers(0, 28))
+        kind = t % 5
+        if kind == 0:  # small integer grid: heavy collinearity and duplicates
+            x = rng.integers(0, 5, n).astype(float)
+            y = rng.integers(0, 5, n).astype(float)
+        elif kind == 1:
+            x, y = rng.random(n), rng.random(n)
+        elif kind == 2:  # points on a few lines
+            s = rng.integers(0, 3, n)
+            w = rng.integers(0, 8, n).astype(float)
+            x = w
+            y = s * w * 0.5 + s
+        elif kind == 3:  # duplicates of a few random points
+            bx, by = rng.random(4), rng.random(4)
+            k = rng.integers(0, 4, n)
+            x, y = bx[k], by[k]
+        else:  # integer points on a circle of radius 5, plus interior
+            ring = [(5, 0), (4, 3), (3, 4), (0, 5), (-3, 4), (-4, 3), (-5, 0), (-4, -3),
+                    (-3, -4), (0, -5), (3, -4), (4, -3)]
+            pts = [ring[i] for i in rng.integers(0, 12, n)]
+            pts += [tuple(rng.integers(-3, 4, 2)) for _ in range(n // 3)]
+            x = np.array([p[0] for p in pts], dtype=float)
+            y = np.array([p[1] for p in pts], dtype=float)
+        yield x, y
+
+
+def test_hull_matches_brute_force():
+    rng = np.random.default_rng(21)
+    for x, y in _tiny_sets(rng, 400):
+        want = E.brute_hull(x, y)
+        got = list(oracle.hull(x, y))
+        assert got == want, (x.tolist(), y.tolist(), got, want)
+
+
+@pytest.mark.parametrize("dist", synth.DISTRIBUTIONS)
+def test_hull_matches_monotone_chain(dist):
+    x, y = synth.points(dist, 20_000, 99)
+    got = list(oracle.hull(x, y))
+    assert got == E.monotone_chain(x, y)
+
+
+def test_hull_matches_monotone_chain_grids():
+    rng = np.random.default_rng(5)
+    for k in (3, 17, 100):
+        x = rng.integers(0, k, 5000).astype(float)
+        y = rng.integers(0, k, 5000).astype(float)
+        assert list(oracle.hull(x, y)) == E.monotone_chain(x, y)
+    # points on a parabola: every point is a vertex and the recursion is deep
+    t = np.arange(-2000, 2000, dtype=float)
+    perm = rng.permutation(t.shape[0])
+    x, y = t[perm], (t * t)[perm]
+    assert list(oracle.hull(x, y)) == E.monotone_chain(x, y)
+
+
+def test_closed_forms():
+    # lattice square {0..k}^2: the four corners, lowest index at each
+    k = 6
+    gx, gy = np.meshgrid(np.arange(k + 1.0), np.arange(k + 1.0))
+    x, y = np.concatenate([gx.ravel(), gx.ravel()]), np.concatenate([gy.ravel(), gy.ravel()])
+    h = oracle.hull(x, y)
+    assert [(x[i], y[i]) for i in h] == [(0, 0), (0, k), (k, k), (k, 0)]
+    assert all(i < (k + 1) ** 2 for i in h)
+    # empty, single, coincident, collinear
+    assert list(oracle.hull(np.array([]), np.array([]))) == []
+    assert list(oracle.hull(np.array([3.0]), np.array([4.0]))) == [0]
+    assert list(oracle.hull(np.full(9, 2.5), np.full(9, -1.0))) == [0]
+    t = np.array([3.0, 1.0, 2.0, 0.0, 5.0, 4.0])
+    assert list(oracle.hull(t, 2 * t + 1)) == [3, 4]
+    # vertical line: lex min is the lowest point, lex max the highest
+    assert list(oracle.hull(np.zeros(5), np.array([2.0, -1.0, 7.0, 3.0, 0.0]))) == [1, 2]
+    # the 12 integer points of the circle x^2 + y^2 = 25 are all vertices
+    ring = [(5, 0), (4, 3), (3, 4), (0, 5), (-3, 4), (-4, 3), (-5, 0), (-4, -3),
+            (-3, -4), (0, -5), (3, -4), (4, -3)]
+    x = np.array([p[0] for p in ring], dtype=float)
+    y = np.array([p[1] for p in ring], dtype=float)
+    h = oracle.hull(x, y)
+    assert len(h) == 12 and (x[h[0]], y[h[0]]) == (-5, 0)
+    assert E.polygon_area2(x, y, h) < 0  # clockwise
+
+
+def test_tie_rule_example():
+    g = json.load(open(os.path.join(GOLDEN, "tie_rule_example.json")))
+    assert list(oracle.hull(np.array(g["x"]), np.array(g["y"]))) == g["hull"]
+
+
+def test_farthest_tie_rule():
+    """Tied farthest points: the one nearest a along a->b, then the lowest
+    index among coincident points."""
+    # a = (0,0), b = (4,0); candidates at height 2 with x = 3, 1, 2, 1
+    x = np.array([0.0, 4.0, 3.0, 1.0, 2.0, 1.0, 2.5])
+    y = np.array([0.0, 0.0, 2.0, 2.0, 2.0, 2.0, 1.0])
+    assert oracle.farthest(x, y, 0, 1, [2, 3, 4, 5, 6]) == 3
+    assert oracle.farthest(x, y, 0, 1, [5, 4, 3, 2]) == 3   # coincident 3, 5: lowest
+    # reversed direction b -> a: the candidates are to the right, so use the
+    # mirrored set below the line; nearest to b = (4,0) start now
+    ym = -y
+    assert oracle.farthest(x, ym, 1, 0, [2, 3, 4, 5, 6]) == 2
+    assert oracle.farthest(x, y, 0, 1, []) == -1
+    # strict maximum wins regardless of projection or index
+    assert oracle.farthest(x, y, 0, 1, [6, 4]) == 4
+
+
+def test_nonfinite_rejected():
+    with pytest.raises(ValueError):
+        oracle.hull(np.array([0.0, np.nan, 1.0]), np.array([0.0, 1.0, 2.0]))
+    with pytest.raises(ValueError):
+        oracle.hull(np.array([0.0, 1.0]), np.array([np.inf, 1.0]))
+
+
+def test_verifier_accepts_and_rejects():
+    x, y = synth.points("disk", 5000, 3)
+    # duplicate a few points with higher indices
+    x = np.concatenate([x, x[:50]])
+    y = np.concatenate([y, y[:50]])
+    h = oracle.hull(x, y)
+    assert oracle.verify(x, y, h) == (0, -1)
+    bad = [
+        h[1:],                                  # start vertex dropped
+        np.delete(h, 3),                        # a vertex dropped
+        np.insert(h, 2, np.int32(len(x) // 2)), # an interior point added
+        h[::-1],                                # counter-clockwise
+        np.roll(h, 1),                          # wrong start
+        np.concatenate([h, h[:1]]),             # vertex repeated
+    ]
+    inside = [i for i in range(50) if i in set(h.tolist())]
+    if inside:
+        hh = h.copy()
+        hh[list(h).index(inside[0])] = len(x) - 50 + inside[0]  # higher-index duplicate
+        bad.append(hh)
+    for b in bad:
+        assert oracle.verify(x, y, b)[0] != 0
+
+
+def test_filter_does_not_change_results():
+    for dist in synth.DISTRIBUTIONS:
+        x, y = synth.points(dist, 3000, 8)
+        oracle.set_filter(True)
+        a = oracle.hull(x, y)
+        oracle.set_filter(False)
+        b = oracle.hull(x, y)
+        assert np.array_equal(a, b)
+
+
+def test_exact_transforms():
+    rng = np.random.default_rng(3)
+    x, y = synth.points("disk", 20_000, 4)
+    h = oracle.hull(x, y)
+    # permutation: the same vertices, indices mapped
+    perm = rng.permutation(x.shape[0])
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.shape[0])
+    hp = oracle.hull(x[perm], y[perm])
+    assert np.array_equal(perm[hp], h)
+    # scaling by powers of two is exact
+    for k in (-40, 7, 300):
+        assert np.array_equal(oracle.hull(x * 2.0 ** k, y * 2.0 ** k), h)
+    # reflection x -> -x: the same vertex set, order reversed, start moved
+    hr = oracle.hull(-x, y)
+    assert set(hr.tolist()) == set(h.tolist())
+    assert oracle.verify(-x, y, hr)[0] == 0
+    # integer translation of integer-valued input
+    xi = rng.integers(-1000, 1000, 20_000).astype(float)
+    yi = rng.integers(-1000, 1000, 20_000).astype(float)
+    hi = oracle.hull(xi, yi)
+    assert np.array_equal(oracle.hull(xi + 12345.0, yi - 777.0), hi)
+
+
+def test_renyi_sulanke_sanity():
+    """Statistical sanity (not parity): hull sizes near their expectations."""
+    x, y = synth.points("disk", 1_000_000, 2)
+    hd = len(oracle.hull(x, y))
+    assert abs(hd / E.renyi_sulanke_disk(1_000_000) - 1.0) < 0.15
+    x, y = synth.points("square", 1_000_000, 1)
+    hs = len(oracle.hull(x, y))
+    assert 0.6 < hs / E.renyi_sulanke_square(1_000_000) < 1.4
+
+
+def test_kuzmin_structure():
+    """Kuzmin (Sec. 5.2, Fig. 3 caption): the second partition removes all
+    remaining points, so the hull is found in two partition levels."""
+    x, y = synth.points("kuzmin", 1_000_000, 4)
+    h, st = oracle.hull(x, y, stats=True)
+    assert st["levels"] <= 3
+    assert st["read"][0] == 1_000_000
+    assert sum(st["written"][1:]) <= 20
+
+
+@pytest.mark.parametrize("dist", ["kuzmin", "disk"])
+def test_paper_byte_model(dist):
+    """Sec. 5.2: 5.6 GB (Kuzmin) and 7.2 GB (disk) at 1e8 points with 16
+    bytes per point read or kept per partition and 8n for the extremes."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_byte_model.json")))
+    n = g["n"]
+    x, y = synth.workload(dist, n)
+    _, st = oracle.hull(x, y, stats=True)
+    got_gb = st["paper_bytes"] / 1e9
+    want = g["bytes_GB"][dist]
+    assert abs(got_gb - want) <= 0.05 * want + 0.05, (got_gb, want)
