@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Benchmark of the level-synchronous planar Quickhull on GB300.
+
+One step = one hull of 1e8 uniform-square points and one hull of 1e8
+uniform-disk points (FP64, SoA, seeds 1 and 2), the paper's 1e8-point
+single-hull pass (Sec. 5.2 sizes) on synthetic stand-ins for its datasets.
+Inputs are resident in HBM before the timed region; each 1.6 GB input is
+larger than L2, so no flush is needed between steps.
+
+Reported (one JSON line on rank 0):
+  value       Gpoints/s over the timed steps (device time, CUDA events);
+  e2e         the same through vq_hull2d_host from pinned host memory,
+              host->device copy and result read-back inside the timing;
+  roofline    the partition kernel (k_k1): paper-model bytes (16 per point
+              classified or kept, Sec. 5.2) over its summed CUDA-event time,
+              against the measured HBM copy bandwidth;
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+--impl reference times the CPU oracle itself (the reference arm).
+With --gpus N (torchrun) every rank runs the same workload on its own GPU
+(replicas; weak scaling) and the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Gpoints/s & % HBM peak per hull; batched hulls/s, p50/p99 vs plain (bit-exact)"
+UNIT = "Gpoints/s"
+WORKLOAD = "single hulls: uniform square + uniform disk, 1e8 FP64 SoA points each (seeds 1, 2)"
+FULL_N = 100_000_000
+# DRAM traffic per partition launch from the committed ncu summary of the
+# current kernel (profiles/); None until a capture of this kernel exists.
+K1_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=FULL_N, help="points per hull (default: the 1e8 workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=30_000_000,
+                    help="points per workload for the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(n_sample: int):
+    """Oracle (sequential C, one core) on the first n_sample points of each
+    workload; returns (Gpoints/s, seconds, sample text)."""
+    import oracle
+    oracle.build()
+    total_pts = 0
+    total_s = 0.0
+    for dist in ("square", "disk"):
+        x, y = synth.workload(dist, FULL_N) if n_sample >= FULL_N else synth.points(
+            dist, n_sample, synth.WORKLOAD_SEEDS[(dist, FULL_N)])
+        t0 = time.perf_counter()
+        oracle.hull(x, y)
+        total_s += time.perf_counter() - t0
+        total_pts += x.shape[0]
+    sample = (f"first {n_sample:,} points of each of the square and disk 1e8 workloads "
+              f"(same seeds), one oracle hull each, 1 thread")
+    return total_pts / total_s / 1e9, total_s, sample
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != self.gpu:
+                    continue
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def run_reference(args, ws, rank):
+    """The reference arm: the CPU oracle, timed on this host."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    m = min(args.n, 10_000_000)
+    data = [synth.points(d, m, synth.WORKLOAD_SEEDS[(d, FULL_N)]) for d in ("square", "disk")]
+    for _ in range(args.warmup):
+        for x, y in data:
+            oracle.hull(x, y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for x, y in data:
+            oracle.hull(x, y)
+    sec = time.perf_counter() - t0
+    pts = 2 * m * args.steps
+    value = pts / sec / 1e9
+    sample = f"first {m:,} points of each of the square and disk 1e8 workloads per step, 1 thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_points_per_hull": m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2510_09417_gb300 as vq
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vq.load()
+    n = args.n
+    if n == FULL_N:
+        data = [synth.workload(d, n) for d in ("square", "disk")]
+    else:
+        data = [synth.points(d, n, synth.WORKLOAD_SEEDS[(d, FULL_N)]) for d in ("square", "disk")]
+    dev = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in data]
+    outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in dev]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        hs = []
+        for (xd, yd), o in zip(dev, outs):
+            hs.append(vq.vq_hull2d(xd, yd, o, stream=stream).shape[0])
+        return hs
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        hull_sizes = step()
+    vq.vq_set_config(profile=1)
+    vq.vq_profile_read(reset=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        hull_sizes = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = vq.vq_profile_read(reset=True)
+    vq.vq_set_config(profile=0)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    pts_step = 2 * n * ws
+    value = pts_step * args.steps / (ms_max / 1e3) / 1e9
+
+    # roofline of the partition kernel: paper-model bytes / event time
+    peak, peak_kind = peaks()
+    k1_bytes = 16.0 * (prof["k1_points_read"] + prof["k1_points_kept"])
+    k1_s = prof["k1_ms"] / 1e3
+    achieved = k1_bytes / k1_s / 1e9 if k1_s > 0 else 0.0
+    traffic = K1_TRAFFIC_BYTES_PER_LAUNCH
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_k1 (fused classify + compact + argmax)",
+                "bytes_per_launch": k1_bytes / max(prof["k1_launches"], 1),
+                "ms_per_launch": prof["k1_ms"] / max(prof["k1_launches"], 1)}
+
+    # end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        pinned = [(torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()) for x, y in data]
+        hbuf = [np.empty(n, dtype=np.int32) for _ in pinned]
+
+        def e2e_step():
+            return [vq.vq_hull2d_host(px.numpy(), py.numpy(), hull_idx=hb).shape[0]
+                    for (px, py), hb in zip(pinned, hbuf)]
+
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ksteps = max(1, min(args.steps, 5))
+        for _ in range(ksteps):
+            hs = e2e_step()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        sec_t = torch.tensor([sec], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(sec_t, op=dist.ReduceOp.MAX)
+        sec = float(sec_t.item())
+        e2e = {"value": pts_step * ksteps / sec / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 16 * n, "d2h_bytes_per_step": 4 * int(sum(hs)),
+               "steps": ksteps, "api": "vq_hull2d_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and ws == 1:
+        m = min(args.cpu_sample, n)
+        rate, sec, sample = cpu_oracle_rate(m)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": sec}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points_per_hull": n, "hulls_per_step": 2,
+                       "l2": "no flush: each input (1.6 GB at 1e8 points) exceeds L2",
+                       "parallelism": f"replicas x{ws}", "hull_sizes": hull_sizes},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(prof["launches"]), "clocks": clk,
+            "detail": {"profile": prof,
+                       "paper_model_GBps": (8.0 * 2 * n * args.steps + k1_bytes) / (ms_max / 1e3) / 1e9},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

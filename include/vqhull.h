@@ -1,0 +1,195 @@
+/*
+ * vqhull.h -- C ABI of libvqhull, a GB300 (sm_103a) planar convex hull
+ * built on the level-synchronous subset extraction of the VQhull paper
+ * (Quickhull, arxiv 2510.09417).
+ *
+ * The result of every hull call is the one defined by Alg. 1 (Sec. 2.1):
+ * the vertices H of the convex hull of the input points, in clockwise
+ * order (y axis up), starting at the leftmost point.  Readings of what the
+ * paper leaves open, applied throughout:
+ *   - leftmost / rightmost are the lexicographic (x, then y) minimum and
+ *     maximum;
+ *   - "to the left of" is strict (Sec. 2.1, first display), so points on a
+ *     hull edge are not vertices: only strict (extreme) vertices are listed,
+ *     each coordinate pair once, represented by its lowest input index;
+ *   - the farthest point of Alg. 1 is taken with exact arithmetic; among
+ *     tied points the one nearest the segment's first endpoint, then the
+ *     lowest index;
+ *   - 0 points give an empty hull, coincident points a single vertex, and
+ *     collinear points their two extreme ends.
+ * Predicates are exact for finite coordinates whose nonzero magnitudes lie
+ * in [2^-400, 2^400]; coordinates outside that range are accepted but the
+ * result may then differ from the exact hull.
+ *
+ * Points are FP64 in structure-of-arrays layout (separate x[] and y[]), the
+ * layout of Sec. 4 / Sec. 5.4.  Indices are 0-based int32.
+ *
+ * Memory: device arrays passed in stay owned by the caller and are only
+ * read (the input is never permuted).  The library keeps one workspace per
+ * device (about 45 bytes per input point), grown on demand and reused
+ * across calls; calls on one device are serialised.
+ *
+ * Errors are returned as vq_status values, never raised or trapped.  After
+ * an error the output arrays hold unspecified values.
+ */
+#ifndef VQHULL_H
+#define VQHULL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VQ_OK = 0,
+  VQ_PENDING = 1,             /* server: result not ready yet               */
+  VQ_ERR_INVALID_ARG = -1,    /* null pointer, negative size, bad offsets   */
+  VQ_ERR_NONFINITE = -2,      /* a NaN or infinite coordinate               */
+  VQ_ERR_TOO_LARGE = -3,      /* sizes beyond the int32 index range          */
+  VQ_ERR_NOMEM = -4,          /* device or host allocation failed            */
+  VQ_ERR_CUDA = -5,           /* a CUDA runtime call failed                  */
+  VQ_ERR_TIMEOUT = -6,        /* a bounded device wait expired               */
+  VQ_ERR_BUDGET = -7,         /* server: request larger than the budget      */
+  VQ_ERR_CAPACITY = -8,       /* output capacity or internal table too small */
+  VQ_ERR_NOT_FOUND = -9       /* server: unknown ticket                      */
+} vq_status;
+
+/* Static description of a status code (never NULL). */
+const char* vq_status_string(int status);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int vq_version(void);
+
+/*
+ * Hull of one point set (Alg. 1).
+ *   x, y      device FP64 arrays of n points (caller-owned, read-only)
+ *   n         0 <= n <= 2^31 - 2
+ *   hull_idx  device int32 array with room for n indices (worst case h = n);
+ *             receives the h vertex indices, clockwise from the lexicographic
+ *             minimum
+ *   h         host pointer; receives the vertex count
+ *   stream    cudaStream_t to enqueue on (NULL = legacy default stream); the
+ *             call synchronises it before returning
+ * Returns VQ_OK, VQ_ERR_INVALID_ARG, VQ_ERR_NONFINITE, VQ_ERR_TOO_LARGE,
+ * VQ_ERR_NOMEM, VQ_ERR_CUDA or VQ_ERR_TIMEOUT.
+ */
+vq_status vq_hull2d(const double* x, const double* y, int64_t n, int32_t* hull_idx, int64_t* h,
+                    void* stream);
+
+/*
+ * Hulls of nsets independent point sets in one level-synchronous run.
+ *   x, y          device FP64 arrays holding the sets back to back
+ *   offsets       device int64[nsets + 1]: set s is points
+ *                 offsets[s] .. offsets[s+1]-1; offsets[0] = 0, non-decreasing;
+ *                 empty sets are allowed
+ *   nsets         >= 1; offsets[nsets] + nsets must stay below 2^31
+ *   hull_idx      device int32 with room for offsets[nsets] indices; receives
+ *                 the hulls back to back, each clockwise from its set's
+ *                 lexicographic minimum, with indices LOCAL to the set
+ *   hull_offsets  device int64[nsets + 1]; receives the hulls' boundaries
+ *                 (hull s is hull_idx[hull_offsets[s] .. hull_offsets[s+1]-1])
+ * Synchronises `stream`.  A set with a non-finite coordinate gets an empty
+ * hull and the call returns VQ_ERR_NONFINITE (the other sets are valid).
+ */
+vq_status vq_hull2d_batched(const double* x, const double* y, const int64_t* offsets, int32_t nsets,
+                            int32_t* hull_idx, int64_t* hull_offsets, void* stream);
+
+/*
+ * vq_hull2d on host memory: copies x, y (n doubles each, host; pinned memory
+ * gives the fastest copies) to a library-owned device buffer, runs the hull
+ * and copies the h indices back.  hull_idx_host needs room for n indices.
+ */
+vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, int32_t* hull_idx_host,
+                         int64_t* h, void* stream);
+
+/* Tuning knobs (process-wide; take effect on the next call). */
+typedef struct {
+  int32_t points_per_thread; /* partition kernel: 4, 8 or 16 points per thread */
+  int32_t small_max;         /* segments of <= small_max points (2..1024) are
+                                finished by the shared-memory kernel          */
+  int32_t k1_blocks_per_sm;  /* partition blocks per SM; 0 = occupancy limit  */
+  int32_t profile;           /* 1: time every kernel with CUDA events (see
+                                vq_profile_read); 0: off                     */
+  int64_t timeout_ns;        /* bound of every device-side wait              */
+  int32_t debug_drop_tile;   /* testing: this partition tile never publishes
+                                its look-back status (-1 = off)              */
+  int32_t reserved1;
+} vq_config;
+
+vq_status vq_get_config(vq_config* cfg);
+vq_status vq_set_config(const vq_config* cfg);
+
+/*
+ * Per-level counters of the last call on the current device: for each
+ * partition level l < *levels (at most cap are copied), read[l] points were
+ * classified, kept[l] of them went to a child, in segs[l] segments (the
+ * per-call statistics of Sec. 5.2's byte model).
+ */
+vq_status vq_last_stats(int64_t* levels, int64_t* read, int64_t* kept, int64_t* segs, int32_t cap);
+
+/*
+ * Counters accumulated over the hull calls on the current device since the
+ * last reset.  Kernel times are filled only while vq_config.profile is set;
+ * they are CUDA-event times on the call's stream.
+ */
+typedef struct {
+  int64_t calls;             /* hull calls                                    */
+  int64_t launches;          /* kernels launched by the library               */
+  int64_t k1_launches;       /* partition kernel launches                     */
+  int64_t levels;            /* partition levels run by the level loop        */
+  int64_t k1_points_read;    /* points classified by the partition kernel     */
+  int64_t k1_points_kept;    /* of those, points written to a child           */
+  double k0_ms;              /* extreme-point pass                            */
+  double k1_ms;              /* partition kernel                              */
+  double k2_ms;              /* per-segment finalize                          */
+  double k3_ms;              /* small-segment finisher                        */
+  double k4_ms;              /* ordering                                      */
+  double other_ms;           /* scans, counter resets                         */
+} vq_profile;
+
+vq_status vq_profile_read(vq_profile* out, int32_t reset);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of hull requests                        */
+/* ------------------------------------------------------------------ */
+
+typedef struct vq_server vq_server;
+
+typedef struct {
+  size_t mem_budget_bytes; /* device memory the server may use in total      */
+  int32_t max_inflight;    /* requests resident on the device at once (>= 1) */
+  int32_t device;          /* CUDA device ordinal                            */
+} vq_server_config;
+
+/* Creates a server with its own device pool and a host thread that admits
+ * queued requests as memory frees up and advances all resident requests
+ * together, one partition level per step. */
+vq_status vq_server_create(const vq_server_config* cfg, vq_server** out);
+
+/* Queues a hull of n host points (copied before return; the caller may free
+ * them).  VQ_ERR_BUDGET if the request alone exceeds the memory budget. */
+vq_status vq_server_submit(vq_server* s, const double* x_host, const double* y_host, int64_t n,
+                           uint64_t* ticket);
+
+/* VQ_OK with the result copied to hull_idx_host (room for cap indices; h set),
+ * VQ_PENDING, VQ_ERR_CAPACITY if cap < h, VQ_ERR_NOT_FOUND, or the request's
+ * own error.  A result is released once returned with VQ_OK. */
+vq_status vq_server_poll(vq_server* s, uint64_t ticket, int32_t* hull_idx_host, int64_t cap, int64_t* h);
+
+/* As vq_server_poll, waiting up to timeout_ms (< 0: no limit). */
+vq_status vq_server_wait(vq_server* s, uint64_t ticket, int32_t* hull_idx_host, int64_t cap, int64_t* h,
+                         int32_t timeout_ms);
+
+/* Latency percentiles (submit to completion) and throughput so far. */
+vq_status vq_server_stats(vq_server* s, double* p50_ms, double* p99_ms, double* hulls_per_s);
+
+/* Stops the server thread and frees its memory; pending requests are dropped. */
+void vq_server_destroy(vq_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VQHULL_H */

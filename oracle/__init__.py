@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 from concurrent.futures import ThreadPoolExecutor
@@ -22,7 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vq_oracle.c")
-_LIB = os.path.join(_HERE, "liborc.so")
+_LIB = os.path.join(_HERE, f"liborc.{platform.machine()}.so")
 _lock = threading.Lock()
 _lib = None
 

@@ -1,0 +1,478 @@
+// vq_api.cu -- host driver and C ABI of libvqhull (single and batched hulls).
+//
+// One call runs Alg. 1 (Sec. 2.1) for all point sets at once, one recursion
+// level per step: extreme points (k_k0*), then per level the fused
+// partition (k_k1), the per-segment finalize (k_k2) and the small-segment
+// finisher (k_k3), until no segment is left; then the vertices are put in
+// clockwise order (k_k4_*).
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/vqhull.h"
+#include "vq_internal.h"
+
+namespace vq {
+
+struct Config {
+  int ppt = 8;
+  int small_max = 1024;
+  int k1_bps = 0;
+  int profile = 0;
+  long long timeout_ns = 2000000000ll;
+  int drop_tile = -1;
+};
+
+static std::mutex g_cfg_mu;
+static Config g_cfg;
+
+static Config get_cfg() {
+  std::lock_guard<std::mutex> g(g_cfg_mu);
+  return g_cfg;
+}
+
+static vq_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return VQ_OK;
+  if (e == cudaErrorMemoryAllocation) return VQ_ERR_NOMEM;
+  return VQ_ERR_CUDA;
+}
+
+#define VQ_CHECK(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_status(e_);      \
+  } while (0)
+
+struct Ctx {
+  std::mutex mu;
+  bool init = false;
+  int device = 0;
+  int sms = 0;
+  char* mem = nullptr;
+  size_t bytes = 0;
+  Ctrl* h_ctrl = nullptr;  // pinned
+  long long* h_total = nullptr;
+  // staging for vq_hull2d_host
+  double* stage = nullptr;
+  int* stage_out = nullptr;
+  long long stage_n = 0;
+  // last call
+  long long* d_stats = nullptr;
+  int last_levels = 0;
+  int bps_cache[17] = {};
+  // profile: accumulated counters and an event pool for kernel timing
+  vq_profile prof{};
+  std::vector<cudaEvent_t> events;
+  std::vector<int> ev_kind;  // one entry per (start, stop) pair
+};
+
+enum { kKindOther = 0, kKindK0, kKindK1, kKindK2, kKindK3, kKindK4 };
+
+// Brackets kernel launches with CUDA events on the call's stream when
+// profiling is on; the times are summed per kernel kind after the call.
+struct Timer {
+  Ctx& c;
+  cudaStream_t st;
+  bool on;
+  int open = -1;
+  Timer(Ctx& c_, cudaStream_t st_, bool on_) : c(c_), st(st_), on(on_) { c.ev_kind.clear(); }
+  cudaError_t begin(int kind) {
+    if (!on) return cudaSuccess;
+    const size_t pair = c.ev_kind.size();
+    while (c.events.size() < 2 * (pair + 1)) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      c.events.push_back(e);
+    }
+    c.ev_kind.push_back(kind);
+    open = (int)pair;
+    return cudaEventRecord(c.events[2 * pair], st);
+  }
+  cudaError_t end() {
+    if (!on || open < 0) return cudaSuccess;
+    const int pair = open;
+    open = -1;
+    return cudaEventRecord(c.events[2 * pair + 1], st);
+  }
+  // call after the stream has been synchronised
+  void collect() {
+    if (!on) return;
+    for (size_t p = 0; p < c.ev_kind.size(); p++) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c.events[2 * p], c.events[2 * p + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      switch (c.ev_kind[p]) {
+        case kKindK0: c.prof.k0_ms += ms; break;
+        case kKindK1: c.prof.k1_ms += ms; break;
+        case kKindK2: c.prof.k2_ms += ms; break;
+        case kKindK3: c.prof.k3_ms += ms; break;
+        case kKindK4: c.prof.k4_ms += ms; break;
+        default: c.prof.other_ms += ms; break;
+      }
+    }
+  }
+};
+
+#define VQ_TIMED(timer, kind, call)          \
+  do {                                       \
+    VQ_CHECK((timer).begin(kind));           \
+    VQ_CHECK(call);                          \
+    VQ_CHECK((timer).end());                 \
+  } while (0)
+
+static Ctx g_ctx[64];
+
+
+static size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Carves the workspace for N points, nsets sets and nkeys order keys.
+// With base == nullptr only the size is computed.
+static size_t layout(Work& w, char* base, long long N, int nsets, long long nkeys, const Config& cfg) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align_up(bytes > 0 ? bytes : 1);
+    return p;
+  };
+  const long long n = N > 0 ? N : 1;
+  for (int b = 0; b < 2; b++) {
+    w.bx[b] = reinterpret_cast<double*>(take(sizeof(double) * n));
+    w.by[b] = reinterpret_cast<double*>(take(sizeof(double) * n));
+    w.bi[b] = reinterpret_cast<int*>(take(sizeof(int) * n));
+  }
+  w.nkeys = nkeys;
+  w.slot = reinterpret_cast<int*>(take(sizeof(int) * (nkeys + 1)));
+  w.bitmap = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * ((nkeys + 31) / 32 + 1)));
+  w.sets = reinterpret_cast<SetRec*>(take(sizeof(SetRec) * nsets));
+  w.k0_tile_start = reinterpret_cast<int*>(take(sizeof(int) * (nsets + 1)));
+  w.capT0 = (int)(n / kK0Tile + nsets + 1);
+  w.k0part = reinterpret_cast<K0Part*>(take(sizeof(K0Part) * w.capT0));
+  w.small_max = cfg.small_max;
+  w.tile = kK1Threads * cfg.ppt;
+  w.capS = (int)(n / (cfg.small_max + 1) + 2);
+  w.capT = (int)(n / w.tile + w.capS + 1);
+  w.capQ = 2 * w.capS + nsets + 16;
+  for (int b = 0; b < 2; b++) {
+    w.segs[b] = reinterpret_cast<SegRec*>(take(sizeof(SegRec) * w.capS));
+    w.geom[b] = reinterpret_cast<SegGeom*>(take(sizeof(SegGeom) * w.capS));
+    w.tile_seg[b] = reinterpret_cast<int*>(take(sizeof(int) * w.capT));
+    w.status[b] = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * w.capT));
+    w.cand[b] = reinterpret_cast<TileCand*>(take(sizeof(TileCand) * w.capT));
+  }
+  w.k3q = reinterpret_cast<SegRec*>(take(sizeof(SegRec) * w.capQ));
+  w.ctrl = reinterpret_cast<Ctrl*>(take(sizeof(Ctrl)));
+  w.stats = reinterpret_cast<long long*>(take(sizeof(long long) * 3 * kMaxLevels));
+  return off;
+}
+
+// scratch for the scans (int64), placed after the layout
+static size_t scan_bytes(long long nkeys, int nsets) {
+  const long long nwords = (nkeys + 31) / 32;
+  const long long nb = (nwords + kK4Words - 1) / kK4Words;
+  const long long a = nb + 1 + scan_tmp_elems(nb + 1);
+  const long long b = scan_tmp_elems((long long)nsets + 1);
+  return align_up(sizeof(long long) * (a > b ? a : b));
+}
+
+static vq_status ctx_init(Ctx& c) {
+  if (c.init) return VQ_OK;
+  VQ_CHECK(cudaGetDevice(&c.device));
+  VQ_CHECK(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device));
+  VQ_CHECK(cudaMallocHost(&c.h_ctrl, sizeof(Ctrl) + 64));
+  c.h_total = reinterpret_cast<long long*>(reinterpret_cast<char*>(c.h_ctrl) + sizeof(Ctrl) + 32);
+  c.init = true;
+  return VQ_OK;
+}
+
+static vq_status ctx_reserve(Ctx& c, size_t bytes) {
+  if (bytes <= c.bytes) return VQ_OK;
+  if (c.mem) {
+    cudaFree(c.mem);
+    c.mem = nullptr;
+    c.bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&c.mem, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&c.mem, bytes);
+    want = bytes;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c.mem = nullptr;
+    return VQ_ERR_NOMEM;
+  }
+  c.bytes = want;
+  return VQ_OK;
+}
+
+static int k1_bps(Ctx& c, const Config& cfg) {
+  if (cfg.k1_bps > 0) return cfg.k1_bps;
+  if (!c.bps_cache[cfg.ppt]) c.bps_cache[cfg.ppt] = k1_blocks_per_sm(cfg.ppt);
+  return c.bps_cache[cfg.ppt];
+}
+
+// The level loop shared by the single and batched entry points.
+static vq_status run(Ctx& c, const double* x, const double* y, const long long* offsets, long long n_single,
+                     int nsets, long long N, int* out, long long* hull_offsets, long long* h_out,
+                     cudaStream_t st) {
+  const Config cfg = get_cfg();
+  const long long nkeys = N + nsets;
+  Work w;
+  memset(&w, 0, sizeof w);
+  const size_t main_bytes = layout(w, nullptr, N, nsets, nkeys, cfg);
+  const size_t total = main_bytes + scan_bytes(nkeys, nsets);
+  vq_status s = ctx_reserve(c, total);
+  if (s != VQ_OK) return s;
+  layout(w, c.mem, N, nsets, nkeys, cfg);
+  long long* scan_tmp = reinterpret_cast<long long*>(c.mem + main_bytes);
+  w.x = x;
+  w.y = y;
+  w.offsets = offsets;
+  w.key_base = nullptr;
+  w.n_single = n_single;
+  w.nsets = nsets;
+  w.N = (int)N;
+  w.timeout_ns = cfg.timeout_ns;
+  w.drop_tile = cfg.drop_tile;
+  c.d_stats = w.stats;
+
+  const long long launches0 = kernels_launched();
+  Timer tm(c, st, cfg.profile != 0);
+  VQ_CHECK(tm.begin(kKindOther));
+  VQ_CHECK(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
+  VQ_CHECK(cudaMemsetAsync(w.stats, 0, sizeof(long long) * 3 * kMaxLevels, st));
+  VQ_CHECK(cudaMemsetAsync(w.bitmap, 0, sizeof(unsigned) * ((nkeys + 31) / 32 + 1), st));
+  VQ_CHECK(launch_seed(w, st));
+  VQ_CHECK(scan_exclusive_i32(w.k0_tile_start, (long long)nsets + 1, reinterpret_cast<int*>(scan_tmp), st));
+  VQ_CHECK(tm.end());
+  VQ_CHECK(tm.begin(kKindK0));
+  VQ_CHECK(launch_k0(w, c.sms * 8, st));
+  VQ_CHECK(launch_k0_finalize(w, st));
+  VQ_CHECK(tm.end());
+
+  const int bps = k1_bps(c, cfg);
+  int level = 0;
+  int levels_run = 0;
+  for (;; level++) {
+    VQ_TIMED(tm, kKindOther, launch_prologue(w, level, st));
+    VQ_TIMED(tm, kKindK1, launch_k1(w, level, cfg.ppt, c.sms * bps, st));
+    c.prof.k1_launches++;
+    VQ_TIMED(tm, kKindK2, launch_k2(w, level, c.sms * 8, st));
+    VQ_TIMED(tm, kKindK3, launch_k3(w, c.sms * 2, st));
+    VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    VQ_CHECK(cudaStreamSynchronize(st));
+    levels_run = level + 1;
+    if (c.h_ctrl->err & kErrFatal) break;
+    if (c.h_ctrl->k1_segs[(level + 1) & 1] == 0) break;
+    if (level > N + 1) {  // every level removes at least one point per segment
+      c.h_ctrl->err |= kErrInternal;
+      break;
+    }
+  }
+  c.last_levels = levels_run;
+  VQ_TIMED(tm, kKindK4, launch_order(w, out, hull_offsets, &w.ctrl->total, scan_tmp, st));
+  VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  VQ_CHECK(cudaStreamSynchronize(st));
+  tm.collect();
+  c.prof.calls++;
+  c.prof.levels += levels_run;
+  c.prof.launches += kernels_launched() - launches0;
+  c.prof.k1_points_read += c.h_ctrl->k1_read;
+  c.prof.k1_points_kept += c.h_ctrl->k1_kept;
+  const unsigned err = c.h_ctrl->err;
+  if (c.h_ctrl->dbg_site)
+    fprintf(stderr, "vqhull: bounds check %d failed (value %lld), level loop ran %d levels\n", c.h_ctrl->dbg_site,
+            c.h_ctrl->dbg_val, levels_run);
+  if (h_out) *h_out = c.h_ctrl->total;
+  if (err & kErrBadOffsets) return VQ_ERR_INVALID_ARG;
+  if (err & kErrTimeout) return VQ_ERR_TIMEOUT;
+  if (err & (kErrCapacity | kErrInternal)) return VQ_ERR_CAPACITY;
+  if (err & kErrNonfinite) return VQ_ERR_NONFINITE;
+  return VQ_OK;
+}
+
+static Ctx* current_ctx(vq_status& s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    s = VQ_ERR_CUDA;
+    return nullptr;
+  }
+  s = VQ_OK;
+  return &g_ctx[dev];
+}
+
+}  // namespace vq
+
+using namespace vq;
+
+
+extern "C" {
+
+const char* vq_status_string(int status) {
+  switch (status) {
+    case VQ_OK: return "ok";
+    case VQ_PENDING: return "pending";
+    case VQ_ERR_INVALID_ARG: return "invalid argument";
+    case VQ_ERR_NONFINITE: return "non-finite coordinate";
+    case VQ_ERR_TOO_LARGE: return "too many points for int32 indices";
+    case VQ_ERR_NOMEM: return "out of memory";
+    case VQ_ERR_CUDA: return "CUDA error";
+    case VQ_ERR_TIMEOUT: return "device wait timed out";
+    case VQ_ERR_BUDGET: return "request exceeds the memory budget";
+    case VQ_ERR_CAPACITY: return "capacity exceeded";
+    case VQ_ERR_NOT_FOUND: return "unknown ticket";
+    default: return "unknown status";
+  }
+}
+
+int vq_version(void) { return 100; }
+
+vq_status vq_hull2d(const double* x, const double* y, int64_t n, int32_t* hull_idx, int64_t* h, void* stream) {
+  if (!h || n < 0) return VQ_ERR_INVALID_ARG;
+  *h = 0;
+  if (n == 0) return VQ_OK;
+  if (!x || !y || !hull_idx) return VQ_ERR_INVALID_ARG;
+  if (n > (int64_t)INT_MAX - 2) return VQ_ERR_TOO_LARGE;
+  vq_status s;
+  Ctx* c = current_ctx(s);
+  if (!c) return s;
+  std::lock_guard<std::mutex> g(c->mu);
+  if ((s = ctx_init(*c)) != VQ_OK) return s;
+  long long hh = 0;
+  s = run(*c, x, y, nullptr, n, 1, n, hull_idx, nullptr, &hh, static_cast<cudaStream_t>(stream));
+  *h = hh;
+  return s;
+}
+
+vq_status vq_hull2d_batched(const double* x, const double* y, const int64_t* offsets, int32_t nsets,
+                            int32_t* hull_idx, int64_t* hull_offsets, void* stream) {
+  if (!offsets || !hull_offsets || nsets < 1) return VQ_ERR_INVALID_ARG;
+  vq_status s;
+  Ctx* c = current_ctx(s);
+  if (!c) return s;
+  std::lock_guard<std::mutex> g(c->mu);
+  if ((s = ctx_init(*c)) != VQ_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  long long N = 0;
+  VQ_CHECK(cudaMemcpyAsync(c->h_total, offsets + nsets, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  VQ_CHECK(cudaStreamSynchronize(st));
+  N = *c->h_total;
+  if (N < 0) return VQ_ERR_INVALID_ARG;
+  if (N + nsets > (long long)INT_MAX - 2) return VQ_ERR_TOO_LARGE;
+  if (N > 0 && (!x || !y || !hull_idx)) return VQ_ERR_INVALID_ARG;
+  return run(*c, x, y, reinterpret_cast<const long long*>(offsets), 0, nsets, N, hull_idx,
+             reinterpret_cast<long long*>(hull_offsets), nullptr, st);
+}
+
+vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, int32_t* hull_idx_host,
+                         int64_t* h, void* stream) {
+  if (!h || n < 0) return VQ_ERR_INVALID_ARG;
+  *h = 0;
+  if (n == 0) return VQ_OK;
+  if (!x_host || !y_host || !hull_idx_host) return VQ_ERR_INVALID_ARG;
+  if (n > (int64_t)INT_MAX - 2) return VQ_ERR_TOO_LARGE;
+  vq_status s;
+  Ctx* c = current_ctx(s);
+  if (!c) return s;
+  std::lock_guard<std::mutex> g(c->mu);
+  if ((s = ctx_init(*c)) != VQ_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->stage_n < n) {
+    if (c->stage) cudaFree(c->stage);
+    if (c->stage_out) cudaFree(c->stage_out);
+    c->stage = nullptr;
+    c->stage_out = nullptr;
+    c->stage_n = 0;
+    if (cudaMalloc(&c->stage, sizeof(double) * 2 * n) != cudaSuccess ||
+        cudaMalloc(&c->stage_out, sizeof(int) * n) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->stage) cudaFree(c->stage);
+      c->stage = nullptr;
+      c->stage_out = nullptr;
+      return VQ_ERR_NOMEM;
+    }
+    c->stage_n = n;
+  }
+  VQ_CHECK(cudaMemcpyAsync(c->stage, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  VQ_CHECK(cudaMemcpyAsync(c->stage + n, y_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  long long hh = 0;
+  s = run(*c, c->stage, c->stage + n, nullptr, n, 1, n, c->stage_out, nullptr, &hh, st);
+  if (s != VQ_OK && s != VQ_ERR_NONFINITE) return s;
+  *h = hh;
+  if (hh > 0) {
+    VQ_CHECK(cudaMemcpyAsync(hull_idx_host, c->stage_out, sizeof(int) * hh, cudaMemcpyDeviceToHost, st));
+    VQ_CHECK(cudaStreamSynchronize(st));
+  }
+  return s;
+}
+
+vq_status vq_get_config(vq_config* cfg) {
+  if (!cfg) return VQ_ERR_INVALID_ARG;
+  const Config c = get_cfg();
+  memset(cfg, 0, sizeof *cfg);
+  cfg->points_per_thread = c.ppt;
+  cfg->small_max = c.small_max;
+  cfg->k1_blocks_per_sm = c.k1_bps;
+  cfg->profile = c.profile;
+  cfg->timeout_ns = c.timeout_ns;
+  cfg->debug_drop_tile = c.drop_tile;
+  return VQ_OK;
+}
+
+vq_status vq_set_config(const vq_config* cfg) {
+  if (!cfg) return VQ_ERR_INVALID_ARG;
+  if (cfg->points_per_thread != 4 && cfg->points_per_thread != 8 && cfg->points_per_thread != 16)
+    return VQ_ERR_INVALID_ARG;
+  if (cfg->small_max < 2 || cfg->small_max > kK3Cap) return VQ_ERR_INVALID_ARG;
+  if (cfg->k1_blocks_per_sm < 0 || cfg->k1_blocks_per_sm > 32) return VQ_ERR_INVALID_ARG;
+  if (cfg->timeout_ns <= 0) return VQ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(g_cfg_mu);
+  g_cfg.ppt = cfg->points_per_thread;
+  g_cfg.small_max = cfg->small_max;
+  g_cfg.k1_bps = cfg->k1_blocks_per_sm;
+  g_cfg.profile = cfg->profile ? 1 : 0;
+  g_cfg.timeout_ns = cfg->timeout_ns;
+  g_cfg.drop_tile = cfg->debug_drop_tile;
+  return VQ_OK;
+}
+
+vq_status vq_last_stats(int64_t* levels, int64_t* read, int64_t* kept, int64_t* segs, int32_t cap) {
+  if (!levels || cap < 0) return VQ_ERR_INVALID_ARG;
+  vq_status s;
+  Ctx* c = current_ctx(s);
+  if (!c) return s;
+  std::lock_guard<std::mutex> g(c->mu);
+  *levels = 0;
+  if (!c->init || !c->d_stats) return VQ_OK;
+  std::vector<long long> buf(3 * kMaxLevels);
+  VQ_CHECK(cudaMemcpy(buf.data(), c->d_stats, sizeof(long long) * 3 * kMaxLevels, cudaMemcpyDeviceToHost));
+  int L = 0;
+  for (int l = 0; l < kMaxLevels; l++)
+    if (buf[2 * kMaxLevels + l] > 0) L = l + 1;
+  *levels = L;
+  for (int l = 0; l < L && l < cap; l++) {
+    if (read) read[l] = buf[l];
+    if (kept) kept[l] = buf[kMaxLevels + l];
+    if (segs) segs[l] = buf[2 * kMaxLevels + l];
+  }
+  return VQ_OK;
+}
+
+vq_status vq_profile_read(vq_profile* out, int32_t reset) {
+  vq_status s;
+  Ctx* c = current_ctx(s);
+  if (!c) return s;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (out) *out = c->prof;
+  if (reset) memset(&c->prof, 0, sizeof c->prof);
+  return VQ_OK;
+}
+
+}  // extern "C"

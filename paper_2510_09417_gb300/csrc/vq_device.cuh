@@ -1,0 +1,531 @@
+// vq_device.cuh -- device-side records and exact predicates for the
+// level-synchronous planar Quickhull (VQhull, arxiv 2510.09417).
+//
+// The predicates are the two tests of Sec. 2.1:
+//   left-of      : (px-ux)(qy-uy) > (py-uy)(qx-ux), i.e. orient(p,q,u) > 0
+//   farther-than : (qy-py)(ux-u'x) < (qx-px)(uy-u'y), i.e. (q-p) x (u-u') > 0
+// evaluated exactly in three tiers:
+//   1. FP32 on coordinates truncated to 24 significant bits by integer ops
+//      (no FP64 instruction), with a per-point error bound derived below;
+//   2. FP64 with Shewchuk's bound (3 + 16 eps) eps (|t1| + |t2|), eps = 2^-53
+//      ("Adaptive Precision Floating-Point Arithmetic and Fast Robust
+//      Geometric Predicates", 1997, Sec. 4);
+//   3. exact expansion arithmetic: TwoProduct by FMA and Grow-Expansion
+//      (Shewchuk 1997, Thm. 10) over the products of raw coordinates.
+// Exactness holds for finite inputs whose nonzero magnitudes lie in
+// [2^-400, 2^400]; the FP32 tier is only used on point sets with all
+// |coordinates| < 2^40 (flag computed by the extreme-point pass).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vq {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxLevels = 512;
+
+// error bits in Ctrl::err
+constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kErrNonfinite = 2u;
+constexpr unsigned kErrCapacity = 4u;
+constexpr unsigned kErrInternal = 8u;
+constexpr unsigned kErrBadOffsets = 16u;
+constexpr unsigned kErrFatal = kErrTimeout | kErrCapacity | kErrInternal | kErrBadOffsets;
+
+// segment flags
+constexpr int kSegFast = 1;       // FP32 tier allowed (all |coords| < 2^40)
+constexpr int kSegSrcInput = 2;   // points still in the caller's arrays (level 0)
+constexpr int kSegSrcBuf1 = 4;    // points in ping-pong buffer 1 (else buffer 0)
+
+// look-back status words: 2 flag bits, 31-bit left count, 31-bit right count
+constexpr unsigned long long kStAgg = 1ull << 62;
+constexpr unsigned long long kStInc = 2ull << 62;
+constexpr unsigned long long kStFlagMask = 3ull << 62;
+constexpr unsigned long long kCnt31 = 0x7fffffffull;
+
+__host__ __device__ inline unsigned long long st_pack(unsigned long long l, unsigned long long r) {
+  return (l << 31) | r;
+}
+
+// Control block: counters shared by the kernels of one call.
+struct Ctrl {
+  unsigned int err;
+  int k1_ticket;
+  int k1_segs[2];     // K1 segments per level parity
+  int k1_tiles[2];    // K1 tiles per level parity
+  int k3_count;       // small-segment queue length
+  int k0_tiles;       // tiles of the extreme pass
+  int k0_ticket;
+  int level;
+  unsigned long long emitted;
+  long long nonfinite_set;  // first set with a non-finite coordinate
+  long long total;          // vertices over all sets (written by the ordering)
+  long long k1_read;        // points classified by the partition kernel
+  long long k1_kept;        // of those, points written to a child
+  int dbg_site;             // checked builds: first failed bounds check
+  int dbg_pad;
+  long long dbg_val;        // checked builds: the offending value
+};
+
+// A live segment: points off .. off+len-1 of its source buffer, hull edge
+// a->b, farthest point r (global indices).  Children are a->r and r->b.
+struct SegRec {
+  long long shift;  // order key of buffer position pos is pos + 1 + shift
+  int off;
+  int len;
+  int a, b, r;
+  int set_off;      // first global index of the point set (for set-local output)
+  int level;        // partition level of this segment
+  int tile_base;
+  int ntiles;
+  int flags;
+};
+
+// Per-segment constants of the FP32 tier and the exact endpoints.
+// Line 1 is a->r (left child), line 2 is r->b (right child).
+struct SegGeom {
+  double ax, ay, rx, ry, bx, by;
+  float o1x, o1y, o2x, o2y;  // origins: truncated a and r (same conversion as points)
+  float d1x, d1y, d2x, d2y;  // rounded r-a and b-r
+  float k1, c1, k2, c2;      // error bound: E = k*(|ux~|+|uy~|) + c + 2^-22 |d~|
+};
+
+struct SetRec {
+  long long shift;  // key(pos) = pos + 1 + shift; key of p = off + shift
+  int off;
+  int len;
+  int flags;
+  int p, q;
+  int pad;
+};
+
+// Tile winners of the fused argmax, for the left (0) and right (1) child.
+struct TileCand {
+  int idx[2];
+  double lo[2];  // bounds of the winner's orient w.r.t. the child's line
+  double hi[2];
+};
+
+struct K0Part {
+  long long minx, miny, maxx, maxy;  // ordered-integer keys
+  int mini, maxi;
+  int flags;  // bit0 nonfinite, bit1 out of FP32 range
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
+  *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+
+// Doubles as signed integers with the same order; -0 and +0 map to 0.
+__device__ __forceinline__ long long order_key(double v) {
+  long long b = __double_as_longlong(v);
+  return b >= 0 ? b : -(b & 0x7fffffffffffffffll);
+}
+
+// FP64 -> FP32 by integer ops: keep the sign, clamp magnitudes below
+// 2^-126 to 2^-126, keep the top 23 fraction bits (truncation), rebias the
+// exponent.  For 2^-126 <= |v| < 2^128 the result is v truncated to 24
+// significant bits: |v~ - v| < 2^-23 |v|.  Below 2^-126, |v~ - v| < 2^-125.
+__device__ __forceinline__ float trunc_f32(double v) {
+  const unsigned lo = static_cast<unsigned>(__double2loint(v));
+  const unsigned hi = static_cast<unsigned>(__double2hiint(v));
+  const unsigned mag = max(hi & 0x7fffffffu, 0x38100000u);
+  const unsigned f = __funnelshift_l(lo, mag, 3) - 0xC0000000u;  // (1023 - 127) << 23, mod 2^32
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+// ---------------------------------------------------------------------------
+// Tier 1: FP32 orient with a rigorous error bound.
+//
+// With u~, o~ the truncated point and origin (|w~ - w| <= 2^-23|w| + 2^-125),
+// D~ = fl32(D) for the exact direction D (|D~ - D| <= 2^-23 |D| + 2^-149),
+// t~ = fl(ux~ - ox~), s~ = fl(uy~ - oy~), p = fl(Dy~ t~),
+// d~ = fl(Dx~ s~ - p) (one FMA), one finds with rho >= (1 + 2^-22) max|D~|
+//   |d~ - d| <= 3.01 * 2^-23 rho (|ux|+|uy|+|ox|+|oy|) + 2^-23.99 |d~| + rho 2^-122 + 2^-104,
+// and |ux| + |uy| <= (1 + 2^-22)(|ux~| + |uy~|) + 2^-124.
+// The bound used, E = k (|ux~|+|uy~|) + c + 2^-22 |d~| with
+// k = 4 * 2^-23 rho and c = 4 * 2^-23 rho (|ox|+|oy|) + rho 2^-100 + 2^-100,
+// is evaluated with upward rounding and covers it with margin, as long as
+// all |coordinates| < 2^40 (so nothing overflows FP32).
+// ---------------------------------------------------------------------------
+
+struct LineF {
+  float ox, oy, dx, dy, k, c;
+};
+
+__device__ __forceinline__ void orient_f32(const LineF& L, float ux, float uy, float m, float& d,
+                                           float& e) {
+  const float t = __fsub_rn(ux, L.ox);
+  const float s = __fsub_rn(uy, L.oy);
+  const float p = __fmul_rn(L.dy, t);
+  d = __fmaf_rn(L.dx, s, -p);
+  e = __fmaf_ru(fabsf(d), 0x1p-22f, __fmaf_ru(L.k, m, L.c));
+}
+
+// ---------------------------------------------------------------------------
+// Tier 2: FP64 with separately rounded operations (never contracted).
+// ---------------------------------------------------------------------------
+
+constexpr double kEps = 1.1102230246251565404e-16;  // 2^-53
+constexpr double kCcwErr = (3.0 + 16.0 * kEps) * kEps;
+
+// sign of (p1-p0) x (q1-q0) if the filter settles it (*sure = true).
+// Also returns the rounded value and its error bound.
+__device__ __forceinline__ int cross_f64(double p0x, double p0y, double p1x, double p1y, double q0x,
+                                         double q0y, double q1x, double q1y, double& det,
+                                         double& bound, bool& sure) {
+  const double t1 = __dmul_rn(__dsub_rn(p1x, p0x), __dsub_rn(q1y, q0y));
+  const double t2 = __dmul_rn(__dsub_rn(p1y, p0y), __dsub_rn(q1x, q0x));
+  det = __dsub_rn(t1, t2);
+  bound = __dmul_ru(kCcwErr, __dadd_ru(fabs(t1), fabs(t2)));
+  if (det > bound) { sure = true; return 1; }
+  if (-det > bound) { sure = true; return -1; }
+  if (bound == 0.0 && det == 0.0) { sure = true; return 0; }
+  sure = false;
+  return 0;
+}
+
+__device__ __forceinline__ int dot_f64(double p0x, double p0y, double p1x, double p1y, double q0x,
+                                       double q0y, double q1x, double q1y, bool& sure) {
+  const double t1 = __dmul_rn(__dsub_rn(p1x, p0x), __dsub_rn(q1x, q0x));
+  const double t2 = __dmul_rn(__dsub_rn(p1y, p0y), __dsub_rn(q1y, q0y));
+  const double det = __dadd_rn(t1, t2);
+  const double bound = __dmul_ru(kCcwErr, __dadd_ru(fabs(t1), fabs(t2)));
+  if (det > bound) { sure = true; return 1; }
+  if (-det > bound) { sure = true; return -1; }
+  if (bound == 0.0 && det == 0.0) { sure = true; return 0; }
+  sure = false;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Tier 3: exact expansion arithmetic (rare path, kept out of line).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& err) {
+  s = __dadd_rn(a, b);
+  const double bv = __dsub_rn(s, a);
+  const double av = __dsub_rn(s, bv);
+  err = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+}
+
+// sign( sum_k sg_k a_k b_k ), n <= 8.  Rare path: loops are kept rolled and
+// the expansion lives in local memory.  Like every helper here it is
+// inlined: the kernels make no device-function calls.
+static __device__ __forceinline__ int exact_sum_sign(int n, const double* a, const double* b, const int* sg) {
+  double e[16];
+  int m = 0;
+#pragma unroll 1
+  for (int k = 0; k < 2 * n; k++) {
+    const int t = k >> 1;
+    const double hi = __dmul_rn(a[t], b[t]);
+    double q = (k & 1) ? hi : __fma_rn(a[t], b[t], -hi);  // exact product error, then the product
+    if (sg[t] < 0) q = -q;
+#pragma unroll 1
+    for (int i = 0; i < m; i++) {  // Grow-Expansion
+      double sum, h;
+      two_sum(q, e[i], sum, h);
+      e[i] = h;
+      q = sum;
+    }
+    e[m++] = q;
+  }
+#pragma unroll 1
+  for (int i = m - 1; i >= 0; i--)
+    if (e[i] != 0.0) return e[i] > 0.0 ? 1 : -1;
+  return 0;
+}
+
+// orient(a,b,c) = (b-a) x (c-a) = bx cy - bx ay - ax cy - by cx + by ax + ay cx
+static __device__ __forceinline__ int exact_orient_sign(double ax, double ay, double bx, double by, double cx,
+                                              double cy) {
+  const double A[6] = {bx, bx, ax, by, by, ay};
+  const double B[6] = {cy, ay, cy, cx, ax, cx};
+  const int S[6] = {1, -1, -1, -1, 1, 1};
+  return exact_sum_sign(6, A, B, S);
+}
+
+static __device__ __forceinline__ int exact_cross_sign(double p0x, double p0y, double p1x, double p1y,
+                                             double q0x, double q0y, double q1x, double q1y) {
+  const double A[8] = {p1x, p1x, p0x, p0x, p1y, p1y, p0y, p0y};
+  const double B[8] = {q1y, q0y, q1y, q0y, q1x, q0x, q1x, q0x};
+  const int S[8] = {1, -1, -1, 1, -1, 1, 1, -1};
+  return exact_sum_sign(8, A, B, S);
+}
+
+static __device__ __forceinline__ int exact_dot_sign(double p0x, double p0y, double p1x, double p1y,
+                                           double q0x, double q0y, double q1x, double q1y) {
+  const double A[8] = {p1x, p1x, p0x, p0x, p1y, p1y, p0y, p0y};
+  const double B[8] = {q1x, q0x, q1x, q0x, q1y, q0y, q1y, q0y};
+  const int S[8] = {1, -1, -1, 1, 1, -1, -1, 1};
+  return exact_sum_sign(8, A, B, S);
+}
+
+// Exact orient sign via tiers 2 and 3 (used only when tier 1 is unsure).
+static __device__ __forceinline__ int orient_sign_slow(double ax, double ay, double bx, double by, double cx,
+                                                double cy) {
+  double det, bound;
+  bool sure;
+  const int s = cross_f64(ax, ay, bx, by, ax, ay, cx, cy, det, bound, sure);
+  if (sure) return s;
+  return exact_orient_sign(ax, ay, bx, by, cx, cy);
+}
+
+// ---------------------------------------------------------------------------
+// Farthest-point comparison: does u beat v as the farthest point to the left
+// of o->e?  Each candidate carries bounds lo <= orient(o, e, .) <= hi.
+// Order: larger orient; then the smaller projection on e - o (the tied
+// point nearest o); then the lower index.  Bounds decide most pairs; the
+// rest go to the exact tiers.
+// ---------------------------------------------------------------------------
+
+template <typename K>
+struct CandT {
+  double x, y;
+  K lo, hi;
+  int idx;
+};
+
+static __device__ __forceinline__ bool beats_exact(double ox, double oy, double ex, double ey, double ux, double uy, int ui,
+                                         double vx, double vy, int vi) {
+  double det, bound;
+  bool sure;
+  int c = cross_f64(ox, oy, ex, ey, vx, vy, ux, uy, det, bound, sure);
+  if (!sure) c = exact_cross_sign(ox, oy, ex, ey, vx, vy, ux, uy);
+  if (c != 0) return c > 0;
+  int d = dot_f64(ox, oy, ex, ey, vx, vy, ux, uy, sure);
+  if (!sure) d = exact_dot_sign(ox, oy, ex, ey, vx, vy, ux, uy);
+  if (d != 0) return d < 0;
+  return ui < vi;
+}
+
+template <typename K>
+__device__ __forceinline__ bool cand_beats(double ox, double oy, double ex, double ey, const CandT<K>& u,
+                                           const CandT<K>& v) {
+  if (u.idx < 0) return false;
+  if (v.idx < 0) return true;
+  if (u.lo > v.hi) return true;
+  if (v.lo > u.hi) return false;
+  return beats_exact(ox, oy, ex, ey, u.x, u.y, u.idx, v.x, v.y, v.idx);
+}
+
+template <typename K>
+__device__ __forceinline__ CandT<K> cand_none() {
+  CandT<K> c;
+  c.x = 0.0; c.y = 0.0; c.lo = (K)0; c.hi = (K)0; c.idx = -1;
+  return c;
+}
+
+template <typename K>
+__device__ __forceinline__ CandT<K> shfl_xor_cand(const CandT<K>& c, int m) {
+  CandT<K> o;
+  o.x = __shfl_xor_sync(kFull, c.x, m);
+  o.y = __shfl_xor_sync(kFull, c.y, m);
+  o.lo = __shfl_xor_sync(kFull, c.lo, m);
+  o.hi = __shfl_xor_sync(kFull, c.hi, m);
+  o.idx = __shfl_xor_sync(kFull, c.idx, m);
+  return o;
+}
+
+// Warp-wide exact argmax (all lanes get the winner).  The comparison is a
+// strict total order on distinct indices, so the butterfly is consistent.
+template <typename K>
+__device__ __forceinline__ CandT<K> warp_best(double ox, double oy, double ex, double ey, CandT<K> c) {
+#pragma unroll 1
+  for (int m = 16; m >= 1; m >>= 1) {
+    const CandT<K> o = shfl_xor_cand(c, m);
+    if (cand_beats(ox, oy, ex, ey, o, c)) c = o;
+  }
+  return c;
+}
+
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, m));
+  return v;
+}
+
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, m));
+  return v;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Segment geometry for the FP32 tier, from the exact endpoints.
+// ---------------------------------------------------------------------------
+
+__device__ inline LineF make_line(double ox, double oy, double ex, double ey) {
+  LineF L;
+  L.ox = trunc_f32(ox);
+  L.oy = trunc_f32(oy);
+  const double dx = __dsub_rn(ex, ox);
+  const double dy = __dsub_rn(ey, oy);
+  L.dx = __double2float_rn(dx);
+  L.dy = __double2float_rn(dy);
+  // rho >= (1 + 2^-22) max |D~|; the rounding of dx, dy in FP64 (2^-53) is
+  // covered by the factor as well
+  const double rho = fmax(fabs((double)L.dx), fabs((double)L.dy)) * (1.0 + 0x1p-21);
+  L.k = __double2float_ru(4.0 * 0x1p-23 * rho);
+  const double mag = fabs(ox) + fabs(oy);
+  L.c = __double2float_ru(4.0 * 0x1p-23 * rho * mag * (1.0 + 0x1p-20) + rho * 0x1p-100 + 0x1p-100);
+  return L;
+}
+
+__device__ inline void fill_geom(SegGeom& g, double ax, double ay, double bx, double by, double rx,
+                                 double ry) {
+  g.ax = ax; g.ay = ay; g.bx = bx; g.by = by; g.rx = rx; g.ry = ry;
+  const LineF l1 = make_line(ax, ay, rx, ry);
+  const LineF l2 = make_line(rx, ry, bx, by);
+  g.o1x = l1.ox; g.o1y = l1.oy; g.d1x = l1.dx; g.d1y = l1.dy; g.k1 = l1.k; g.c1 = l1.c;
+  g.o2x = l2.ox; g.o2y = l2.oy; g.d2x = l2.dx; g.d2y = l2.dy; g.k2 = l2.k; g.c2 = l2.c;
+}
+
+__device__ __forceinline__ LineF line1_of(const SegGeom& g) {
+  LineF L; L.ox = g.o1x; L.oy = g.o1y; L.dx = g.d1x; L.dy = g.d1y; L.k = g.k1; L.c = g.c1; return L;
+}
+__device__ __forceinline__ LineF line2_of(const SegGeom& g) {
+  LineF L; L.ox = g.o2x; L.oy = g.o2y; L.dx = g.d2x; L.dy = g.d2y; L.k = g.k2; L.c = g.c2; return L;
+}
+
+// ---------------------------------------------------------------------------
+// Classification of one point against a segment (a, r, b):
+// 1 = left of a->r (left child), 2 = left of r->b (right child), 0 = discard.
+// key/err: orient of the point w.r.t. its child's line, with a bound
+// (|key - exact| <= err).  The FAST variant keeps keys in FP32 so the hot
+// loop issues no FP64 instruction unless the filter is inconclusive.
+// ---------------------------------------------------------------------------
+
+template <bool FAST>
+struct KeyOf { typedef double T; };
+template <>
+struct KeyOf<true> { typedef float T; };
+
+__device__ __forceinline__ float key_lo(float k, float e) { return __fsub_rd(k, e); }
+__device__ __forceinline__ double key_lo(double k, double e) { return __dsub_rd(k, e); }
+__device__ __forceinline__ float key_hi(float k, float e) { return __fadd_ru(k, e); }
+__device__ __forceinline__ double key_hi(double k, double e) { return __dadd_ru(k, e); }
+__device__ __forceinline__ float key_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double key_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float warp_max_k(float v) { return warp_max_f(v); }
+__device__ __forceinline__ double warp_max_k(double v) { return warp_max_d(v); }
+template <typename T> __device__ __forceinline__ T key_neg_inf();
+template <> __device__ __forceinline__ float key_neg_inf<float>() { return -INFINITY; }
+template <> __device__ __forceinline__ double key_neg_inf<double>() { return -INFINITY; }
+
+__device__ __forceinline__ int classify_fast(const SegGeom& g, const LineF& l1, const LineF& l2,
+                                             double ux, double uy, float& key, float& err) {
+  const float fx = trunc_f32(ux), fy = trunc_f32(uy);
+  const float m = __fadd_ru(fabsf(fx), fabsf(fy));
+  float d1, e1, d2, e2;
+  orient_f32(l1, fx, fy, m, d1, e1);
+  orient_f32(l2, fx, fy, m, d2, e2);
+  int s1 = d1 > e1 ? 1 : (d1 < -e1 ? -1 : 2);
+  if (s1 == 2) s1 = orient_sign_slow(g.ax, g.ay, g.rx, g.ry, ux, uy);
+  if (s1 > 0) { key = d1; err = e1; return 1; }
+  int s2 = d2 > e2 ? 1 : (d2 < -e2 ? -1 : 2);
+  if (s2 == 2) s2 = orient_sign_slow(g.rx, g.ry, g.bx, g.by, ux, uy);
+  if (s2 > 0) { key = d2; err = e2; return 2; }
+  return 0;
+}
+
+__device__ __forceinline__ int classify_slow(const SegGeom& g, double ux, double uy, double& key,
+                                             double& err) {
+  double d1, b1, d2, b2;
+  bool sure;
+  int s1 = cross_f64(g.ax, g.ay, g.rx, g.ry, g.ax, g.ay, ux, uy, d1, b1, sure);
+  if (!sure) s1 = exact_orient_sign(g.ax, g.ay, g.rx, g.ry, ux, uy);
+  if (s1 > 0) { key = d1; err = b1; return 1; }
+  int s2 = cross_f64(g.rx, g.ry, g.bx, g.by, g.rx, g.ry, ux, uy, d2, b2, sure);
+  if (!sure) s2 = exact_orient_sign(g.rx, g.ry, g.bx, g.by, ux, uy);
+  if (s2 > 0) { key = d2; err = b2; return 2; }
+  return 0;
+}
+
+// Filter-only classification (no calls): returns 0, 1, 2 when the filter
+// settles both signs it needs, 3 when the exact tiers must decide.
+// key/err are set for results 1 and 2.
+__device__ __forceinline__ int classify_filter(const SegGeom&, const LineF& l1, const LineF& l2, double ux,
+                                               double uy, float& key, float& err) {
+  const float fx = trunc_f32(ux), fy = trunc_f32(uy);
+  const float m = __fadd_ru(fabsf(fx), fabsf(fy));
+  float d1, e1;
+  orient_f32(l1, fx, fy, m, d1, e1);
+  if (d1 > e1) { key = d1; err = e1; return 1; }
+  if (!(d1 < -e1)) return 3;
+  float d2, e2;
+  orient_f32(l2, fx, fy, m, d2, e2);
+  if (d2 > e2) { key = d2; err = e2; return 2; }
+  if (!(d2 < -e2)) return 3;
+  return 0;
+}
+__device__ __forceinline__ int classify_filter(const SegGeom& g, const LineF&, const LineF&, double ux, double uy,
+                                               double& key, double& err) {
+  bool sure;
+  const int s1 = cross_f64(g.ax, g.ay, g.rx, g.ry, g.ax, g.ay, ux, uy, key, err, sure);
+  if (!sure) return 3;
+  if (s1 > 0) return 1;
+  const int s2 = cross_f64(g.rx, g.ry, g.bx, g.by, g.rx, g.ry, ux, uy, key, err, sure);
+  if (!sure) return 3;
+  return s2 > 0 ? 2 : 0;
+}
+
+// Exact classification (tiers 2 and 3; out-of-line calls).
+__device__ __forceinline__ int classify_exact(const SegGeom& g, double ux, double uy) {
+  if (orient_sign_slow(g.ax, g.ay, g.rx, g.ry, ux, uy) > 0) return 1;
+  if (orient_sign_slow(g.rx, g.ry, g.bx, g.by, ux, uy) > 0) return 2;
+  return 0;
+}
+
+__device__ __forceinline__ int classify_k(const SegGeom& g, const LineF& l1, const LineF& l2,
+                                          double ux, double uy, float& key, float& err) {
+  return classify_fast(g, l1, l2, ux, uy, key, err);
+}
+__device__ __forceinline__ int classify_k(const SegGeom& g, const LineF&, const LineF&, double ux,
+                                          double uy, double& key, double& err) {
+  return classify_slow(g, ux, uy, key, err);
+}
+
+// Key and bound of a point for one line only (farthest-point search).
+__device__ __forceinline__ void line_key_k(const LineF& L, double, double, double, double, double ux,
+                                           double uy, float& key, float& err) {
+  const float fx = trunc_f32(ux), fy = trunc_f32(uy);
+  const float m = __fadd_ru(fabsf(fx), fabsf(fy));
+  orient_f32(L, fx, fy, m, key, err);
+}
+__device__ __forceinline__ void line_key_k(const LineF&, double ox, double oy, double ex, double ey,
+                                           double ux, double uy, double& key, double& err) {
+  bool sure;
+  cross_f64(ox, oy, ex, ey, ox, oy, ux, uy, key, err, sure);
+}
+
+}  // namespace vq

@@ -1,0 +1,69 @@
+// vq_internal.h -- declarations shared by the kernels and the host driver.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vq_device.cuh"
+
+namespace vq {
+
+constexpr int kK1Threads = 256;
+constexpr int kK0Threads = 256;
+constexpr int kK0Tile = 8192;       // points per extreme-pass tile
+constexpr int kK3Cap = 1024;        // points per warp in the small-segment kernel
+constexpr int kK3Warps = 4;
+constexpr int kK3Stack = 24;
+constexpr int kK4Words = 1024;      // bitmap words per ordering block (256 threads x 4)
+
+// Everything a kernel needs, passed by value.
+struct Work {
+  const double* x;           // caller's points (global index = position)
+  const double* y;
+  const long long* offsets;  // nsets + 1 device offsets, or null (single set of n_single)
+  const long long* key_base; // optional per-set key of p (server); null: off + set
+  long long n_single;
+  int nsets;
+  int N;
+  double* bx[2];
+  double* by[2];
+  int* bi[2];
+  int* slot;
+  unsigned* bitmap;
+  long long nkeys;
+  SetRec* sets;
+  int* k0_tile_start;        // nsets + 1
+  K0Part* k0part;
+  SegRec* segs[2];
+  SegGeom* geom[2];
+  int* tile_seg[2];
+  unsigned long long* status[2];
+  TileCand* cand[2];
+  SegRec* k3q;
+  Ctrl* ctrl;
+  long long* stats;          // [3][kMaxLevels]: points read, points kept, segments
+  int capS, capT, capQ, capT0;
+  int small_max;             // segments with len <= small_max go to the small kernel
+  int tile;                  // K1 tile size
+  long long timeout_ns;
+  int drop_tile;             // test knob: this K1 tile never publishes (-1: none)
+};
+
+// launchers (vq_kernels.cu); all enqueue on `st`
+cudaError_t launch_seed(const Work& w, cudaStream_t st);
+cudaError_t launch_k0(const Work& w, int grid, cudaStream_t st);
+cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st);
+cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st);
+cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st);
+cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st);
+cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st);
+cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long long* total,
+                         long long* tmp, cudaStream_t st);
+cudaError_t scan_exclusive_i32(int* data, long long n, int* tmp, cudaStream_t st);
+cudaError_t scan_exclusive_i64(long long* data, long long n, long long* tmp, cudaStream_t st);
+long long scan_tmp_elems(long long n);
+int k1_blocks_per_sm(int ppt);
+long long kernels_launched();  // kernels launched by this library so far (all devices)
+int k3_smem_bytes();
+
+}  // namespace vq

@@ -1,0 +1,1158 @@
+// vq_kernels.cu -- the kernels of the level-synchronous planar Quickhull.
+//
+// One level of Alg. 1 (Sec. 2.1) is run for every live segment (a, b, r) at
+// once: each point u of the segment is classified as left of a->r (child
+// a->r), left of r->b (child r->b) or discarded (the subset extraction of
+// Sec. 3), the two children are compacted into the other ping-pong buffer
+// (left child forward from the segment start, right child backward from its
+// end, as in the two-ended layout of Alg. 2), and each child's farthest point
+// is found in the same pass (Sec. 4, "Bandwidth considerations").
+//
+// Kernels, in call order:
+//   k_seed / k_k0 / k_k0_finalize  leftmost p and rightmost q per point set
+//                                  (Alg. 1, first two steps), level-0 segments
+//   k_prologue                     per-level counter reset
+//   k_k1                           fused classify + compact + per-tile argmax,
+//                                  offsets by decoupled look-back
+//   k_k2                           per segment: exact cross-tile argmax, emit r,
+//                                  child segments, next level's tile map
+//   k_k3                           segments of <= small_max points, finished
+//                                  whole in shared memory (one warp each)
+//   k_k4_*                         clockwise order of the emitted vertices
+//
+// Hull order.  A vertex r emitted for segment [off, off+len) gets the order
+// key off + nL + 1 + shift: the buffer position between its left child
+// [off, off+nL) and right child [off+len-nR, off+len).  All descendants of
+// the left child get keys inside the left range and those of the right child
+// inside the right range, so sorting by key is the in-order traversal of
+// Alg. 1's recursion, i.e. the clockwise hull.  p gets key off + shift.
+#include <climits>
+
+#include "vq_internal.h"
+
+namespace vq {
+
+static unsigned long long g_launches = 0;
+static inline void count_launch(int k = 1) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+long long kernels_launched() { return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+// ---------------------------------------------------------------------------
+// shared helpers
+// ---------------------------------------------------------------------------
+
+// Checked builds (VQ_CHECKED=1) validate computed indices before use: a
+// failure records its site and value, raises kErrInternal and skips the access.
+#ifdef VQ_CHECKED
+#define VQ_OK_IDX(w, site, v, lo, hi) vq_check_idx((w), (site), (long long)(v), (long long)(lo), (long long)(hi))
+__device__ __forceinline__ bool vq_check_idx(const Work& w, int site, long long v, long long lo, long long hi) {
+  if (v >= lo && v < hi) return true;
+  if (atomicCAS(&w.ctrl->dbg_site, 0, site) == 0) w.ctrl->dbg_val = v;
+  atomicOr(&w.ctrl->err, kErrInternal);
+  return false;
+}
+#else
+#define VQ_OK_IDX(w, site, v, lo, hi) true
+#endif
+
+__device__ __forceinline__ bool fatal(const Work& w) {
+  return (*reinterpret_cast<volatile unsigned*>(&w.ctrl->err) & kErrFatal) != 0;
+}
+
+__device__ __forceinline__ void emit(const Work& w, long long key, int local) {
+  if (!VQ_OK_IDX(w, 1, key, 0, w.nkeys) || !VQ_OK_IDX(w, 2, local, 0, w.N)) return;
+  atomicOr(&w.bitmap[key >> 5], 1u << (unsigned)(key & 31));
+  w.slot[key] = local;
+}
+
+__device__ __forceinline__ void add_stats(const Work& w, int level, long long rd, long long kept) {
+  const int l = level < kMaxLevels ? level : kMaxLevels - 1;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[l]), (unsigned long long)rd);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[kMaxLevels + l]), (unsigned long long)kept);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[2 * kMaxLevels + l]), 1ull);
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+  return v;
+}
+
+// Append a segment for the partition kernel (whole warp): reserve its tiles,
+// write its geometry and the tile -> segment map, clear the tiles' status.
+__device__ void push_k1_warp(const Work& w, int par, SegRec R, int lane) {
+  const int ntiles = (R.len + w.tile - 1) / w.tile;
+  int slot = 0, base = 0;
+  if (lane == 0) {
+    slot = atomicAdd(&w.ctrl->k1_segs[par], 1);
+    base = atomicAdd(&w.ctrl->k1_tiles[par], ntiles);
+  }
+  slot = __shfl_sync(kFull, slot, 0);
+  base = __shfl_sync(kFull, base, 0);
+  if (slot >= w.capS || base > w.capT - ntiles) {
+    if (lane == 0) atomicOr(&w.ctrl->err, kErrCapacity);
+    return;
+  }
+  R.tile_base = base;
+  R.ntiles = ntiles;
+  if (!VQ_OK_IDX(w, 3, R.a, 0, w.N) || !VQ_OK_IDX(w, 4, R.b, 0, w.N) || !VQ_OK_IDX(w, 5, R.r, 0, w.N) ||
+      !VQ_OK_IDX(w, 6, (long long)R.off + R.len, 1, (long long)w.N + 1))
+    return;
+  if (lane == 0) {
+    w.segs[par][slot] = R;
+    SegGeom g;
+    fill_geom(g, w.x[R.a], w.y[R.a], w.x[R.b], w.y[R.b], w.x[R.r], w.y[R.r]);
+    w.geom[par][slot] = g;
+  }
+  for (int i = lane; i < ntiles; i += kWarp) {
+    w.tile_seg[par][base + i] = slot;
+    w.status[par][base + i] = 0ull;
+  }
+}
+
+__device__ __forceinline__ void push_k3(const Work& w, const SegRec& R) {
+  const int i = atomicAdd(&w.ctrl->k3_count, 1);
+  if (i < w.capQ) w.k3q[i] = R;
+  else atomicOr(&w.ctrl->err, kErrCapacity);
+}
+
+// ---------------------------------------------------------------------------
+// Point sets and the extreme pass
+// ---------------------------------------------------------------------------
+
+__global__ void k_seed(Work w) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) {
+    w.k0_tile_start[w.nsets] = 0;
+    w.ctrl->nonfinite_set = LLONG_MAX;
+  }
+  if (s >= w.nsets) return;
+  long long off, end;
+  if (w.offsets) {
+    off = w.offsets[s];
+    end = w.offsets[s + 1];
+  } else {
+    off = 0;
+    end = w.n_single;
+  }
+  if (off < 0 || end < off || end > w.N || (s == 0 && off != 0) ||
+      (s == w.nsets - 1 && end != w.N)) {
+    atomicOr(&w.ctrl->err, kErrBadOffsets);
+    off = 0;
+    end = 0;
+  }
+  SetRec r;
+  r.off = (int)off;
+  r.len = (int)(end - off);
+  r.shift = w.key_base ? w.key_base[s] - off : (long long)s;
+  r.flags = 0;
+  r.p = r.q = -1;
+  r.pad = 0;
+  w.sets[s] = r;
+  w.k0_tile_start[s] = (r.len + kK0Tile - 1) / kK0Tile;
+}
+
+struct LexPt {
+  long long kx, ky;
+  int i;
+};
+
+__device__ __forceinline__ bool lex_min_better(const LexPt& a, const LexPt& b) {
+  return a.kx < b.kx || (a.kx == b.kx && (a.ky < b.ky || (a.ky == b.ky && a.i < b.i)));
+}
+__device__ __forceinline__ bool lex_max_better(const LexPt& a, const LexPt& b) {
+  return a.kx > b.kx || (a.kx == b.kx && (a.ky > b.ky || (a.ky == b.ky && a.i < b.i)));
+}
+__device__ __forceinline__ LexPt shfl_lex(const LexPt& p, int m) {
+  LexPt o;
+  o.kx = __shfl_xor_sync(kFull, p.kx, m);
+  o.ky = __shfl_xor_sync(kFull, p.ky, m);
+  o.i = __shfl_xor_sync(kFull, p.i, m);
+  return o;
+}
+
+// Lexicographic min and max (x, then y, then lowest index) of each tile, as
+// integer comparisons of the coordinates' ordered bit patterns; also flags
+// non-finite values and magnitudes >= 2^40 (outside the FP32 tier's range).
+__global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
+  __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
+  __shared__ int s_fl[kK0Threads / kWarp];
+  const int total = w.k0_tile_start[w.nsets];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = w.nsets - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (w.k0_tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const SetRec S = w.sets[lo];
+    const int j = t - w.k0_tile_start[lo];
+    const int begin = S.off + j * kK0Tile;
+    const int count = min(kK0Tile, S.len - j * kK0Tile);
+    LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
+    int fl = 0;
+#pragma unroll 8
+    for (int l = threadIdx.x; l < count; l += kK0Threads) {
+      const double vx = w.x[begin + l], vy = w.y[begin + l];
+      const LexPt p{order_key(vx), order_key(vy), begin + l};
+      if (lex_min_better(p, mn)) mn = p;
+      if (lex_max_better(p, mx)) mx = p;
+      const unsigned long long ax = (unsigned long long)__double_as_longlong(vx) & 0x7fffffffffffffffull;
+      const unsigned long long ay = (unsigned long long)__double_as_longlong(vy) & 0x7fffffffffffffffull;
+      const unsigned long long am = ax > ay ? ax : ay;
+      fl |= (am >= 0x7ff0000000000000ull ? 1 : 0) | (am >= 0x4270000000000000ull ? 2 : 0);
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      const LexPt a = shfl_lex(mn, m), b = shfl_lex(mx, m);
+      if (lex_min_better(a, mn)) mn = a;
+      if (lex_max_better(b, mx)) mx = b;
+      fl |= __shfl_xor_sync(kFull, fl, m);
+    }
+    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < kK0Threads / kWarp; q++) {
+        if (lex_min_better(s_mn[q], mn)) mn = s_mn[q];
+        if (lex_max_better(s_mx[q], mx)) mx = s_mx[q];
+        fl |= s_fl[q];
+      }
+      K0Part P;
+      P.minx = mn.kx; P.miny = mn.ky; P.mini = mn.i;
+      P.maxx = mx.kx; P.maxy = mx.ky; P.maxi = mx.i;
+      P.flags = fl;
+      P.pad = 0;
+      w.k0part[t] = P;
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per point set: p, q, the set's flags; emit p; make the level-0
+// segment (a = p, b = p, r = q), whose children are p->q (upper, points left
+// of p->q) and q->p (lower), the two calls of Alg. 1's first line.
+__global__ void k_k0_finalize(Work w) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int s = gw; s < w.nsets; s += nw) {
+    SetRec S = w.sets[s];
+    if (S.len == 0) continue;
+    LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
+    int fl = 0;
+    for (int t = w.k0_tile_start[s] + lane; t < w.k0_tile_start[s + 1]; t += kWarp) {
+      const K0Part P = w.k0part[t];
+      const LexPt a{P.minx, P.miny, P.mini}, b{P.maxx, P.maxy, P.maxi};
+      if (lex_min_better(a, mn)) mn = a;
+      if (lex_max_better(b, mx)) mx = b;
+      fl |= P.flags;
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      const LexPt a = shfl_lex(mn, m), b = shfl_lex(mx, m);
+      if (lex_min_better(a, mn)) mn = a;
+      if (lex_max_better(b, mx)) mx = b;
+      fl |= __shfl_xor_sync(kFull, fl, m);
+    }
+    if (fl & 1) {
+      if (lane == 0) {
+        atomicOr(&w.ctrl->err, kErrNonfinite);
+        atomicMin(reinterpret_cast<unsigned long long*>(&w.ctrl->nonfinite_set), (unsigned long long)s);
+      }
+      continue;
+    }
+    const int p = mn.i, q = mx.i;
+    S.p = p;
+    S.q = q;
+    S.flags = (fl & 2) ? 0 : kSegFast;
+    if (lane == 0) {
+      w.sets[s] = S;
+      emit(w, (long long)S.off + S.shift, p - S.off);
+    }
+    if (p == q) continue;  // all points coincide with p
+    SegRec R;
+    R.shift = S.shift;
+    R.off = S.off;
+    R.len = S.len;
+    R.a = p;
+    R.b = p;
+    R.r = q;
+    R.set_off = S.off;
+    R.level = 0;
+    R.tile_base = 0;
+    R.ntiles = 0;
+    R.flags = S.flags | kSegSrcInput;
+    if (S.len <= w.small_max) {
+      if (lane == 0) push_k3(w, R);
+    } else {
+      push_k1_warp(w, 0, R, lane);
+    }
+  }
+}
+
+__global__ void k_prologue(Work w, int level) {
+  const int par = level & 1;
+  w.ctrl->k1_ticket = 0;
+  w.ctrl->k1_segs[par ^ 1] = 0;
+  w.ctrl->k1_tiles[par ^ 1] = 0;
+  if (level > 0) w.ctrl->k3_count = 0;
+  w.ctrl->level = level;
+}
+
+// ---------------------------------------------------------------------------
+// K1: fused classify + compact + per-tile argmax
+// ---------------------------------------------------------------------------
+
+template <int PPT>
+struct K1Smem {
+  SegRec seg;
+  SegGeom geom;
+  int cnt[2][PPT * (kK1Threads / kWarp)];
+  int tot[2];
+  int excl[2];
+  int tile;
+  CandT<double> wc[2][kK1Threads / kWarp];
+};
+
+// staging area of one tile (dynamic shared memory): compacted survivors,
+// left child from the front, right child from the back
+template <int PPT>
+struct K1Stage {
+  static constexpr int TILE = kK1Threads * PPT;
+  static constexpr size_t bytes = (size_t)TILE * (2 * sizeof(double) + sizeof(int));
+};
+
+// Decoupled look-back (Merrill and Garland, "Single-pass Parallel Prefix
+// Scan with Decoupled Look-back", 2016) restarted at every segment: tile t
+// publishes its (left, right) counts, then sums predecessors of the same
+// segment until one with an inclusive prefix.  Waits are bounded by
+// w.timeout_ns; on expiry the error flag is set and false returned.
+__device__ __forceinline__ bool lookback(const Work& w, int par, int t, int first, unsigned long long aggL,
+                                         unsigned long long aggR, long long& exclL, long long& exclR,
+                                         int lane) {
+  unsigned long long* st = w.status[par];
+  exclL = 0;
+  exclR = 0;
+  const bool publish = (t != w.drop_tile);
+  if (t == first) {
+    if (lane == 0 && publish) st_volatile_u64(&st[t], kStInc | st_pack(aggL, aggR));
+    return true;
+  }
+  if (lane == 0 && publish) st_volatile_u64(&st[t], kStAgg | st_pack(aggL, aggR));
+  const unsigned long long t0 = global_ns();
+  int look = t - 1;
+  bool ok = true;
+  for (;;) {
+    const int pos = look - lane;
+    unsigned long long v = 0;
+    if (pos >= first) {
+      v = ld_volatile_u64(&st[pos]);
+      while ((v & kStFlagMask) == 0) {
+        if (global_ns() - t0 > (unsigned long long)w.timeout_ns) { ok = false; break; }
+        __nanosleep(64);
+        v = ld_volatile_u64(&st[pos]);
+      }
+    }
+    ok = __all_sync(kFull, ok);
+    if (!ok) break;
+    const unsigned inc = __ballot_sync(kFull, pos >= first && (v & kStFlagMask) == kStInc);
+    const int stop = inc ? __ffs(inc) - 1 : 31;
+    long long l = 0, r = 0;
+    if (lane <= stop && pos >= first) {
+      l = (long long)((v >> 31) & kCnt31);
+      r = (long long)(v & kCnt31);
+    }
+    exclL += warp_sum_ll(l);
+    exclR += warp_sum_ll(r);
+    if (inc) break;
+    look -= kWarp;
+    if (look < first) { ok = false; break; }  // cannot happen: the first tile is inclusive
+  }
+  if (!ok) {
+    if (lane == 0) atomicOr(&w.ctrl->err, kErrTimeout);
+    return false;
+  }
+  if (lane == 0 && publish)
+    st_volatile_u64(&st[t], kStInc | st_pack((unsigned long long)exclL + aggL, (unsigned long long)exclR + aggR));
+  return true;
+}
+
+// Running exact argmax of one thread: replace the best when the new point
+// beats it (bounds first, exact tiers only when the bounds overlap).
+template <typename K>
+__device__ __forceinline__ void take_best(CandT<K>& b, double ox, double oy, double ex, double ey, double x,
+                                          double y, int idx, K key, K err) {
+  const K lo = key_lo(key, err), hi = key_hi(key, err);
+  if (b.idx >= 0 && hi < b.lo) return;  // clearly nearer the line
+  if (b.idx < 0 || lo > b.hi || beats_exact(ox, oy, ex, ey, x, y, idx, b.x, b.y, b.idx)) {
+    b.x = x; b.y = y; b.lo = lo; b.hi = hi; b.idx = idx;
+  }
+}
+
+template <typename K>
+__device__ __forceinline__ CandT<double> to_double(const CandT<K>& c) {
+  CandT<double> d;
+  d.x = c.x; d.y = c.y; d.lo = (double)c.lo; d.hi = (double)c.hi; d.idx = c.idx;
+  return d;
+}
+
+template <int PPT, bool SRC_INPUT, bool FAST>
+__device__ __forceinline__ void k1_tile(const Work& w, int level, int t, K1Smem<PPT>& sm, double* stx, double* sty,
+                                        int* sti) {
+  typedef typename KeyOf<FAST>::T K;
+  constexpr int T = kK1Threads, W = T / kWarp, TILE = T * PPT;
+  constexpr int PER = PPT * W / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int par = level & 1;
+  const int srcb = (level + 1) & 1, dstb = level & 1;
+  const SegRec& S = sm.seg;
+  const SegGeom& G = sm.geom;
+  const int j = t - S.tile_base;
+  const int begin = S.off + j * TILE;
+  const int count = min(TILE, S.len - j * TILE);
+  const double* __restrict__ sx = SRC_INPUT ? w.x : w.bx[srcb];
+  const double* __restrict__ sy = SRC_INPUT ? w.y : w.by[srcb];
+  const int* __restrict__ si = w.bi[srcb];
+
+  // A: load, classify, running exact argmax per child (each warp reads 32
+  // consecutive points per round)
+  double px[PPT], py[PPT];
+  int pi[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; k++) {
+    const int l = k * T + tid;
+    px[k] = 0.0; py[k] = 0.0; pi[k] = 0;
+    if (l < count && VQ_OK_IDX(w, 7, (long long)begin + l, 0, w.N)) {
+      px[k] = __ldcs(sx + begin + l);
+      py[k] = __ldcs(sy + begin + l);
+      pi[k] = SRC_INPUT ? begin + l : __ldcs(si + begin + l);
+#ifdef VQ_CHECKED
+      if (!VQ_OK_IDX(w, 8, pi[k], 0, w.N)) pi[k] = 0;
+#endif
+    }
+  }
+  // pass 1: filter only, no calls; undecided points are flagged.  Per child
+  // the largest lower bound of the key (farthest-point search) is kept.
+  unsigned cls = 0, und = 0;
+  K lo0 = key_neg_inf<K>(), lo1 = key_neg_inf<K>();
+  const LineF l1 = line1_of(G), l2 = line2_of(G);
+#pragma unroll
+  for (int k = 0; k < PPT; k++) {
+    const int l = k * T + tid;
+    if (l < count) {
+      K key, err;
+      const int c = classify_filter(G, l1, l2, px[k], py[k], key, err);
+      if (c == 3) {
+        und |= 1u << k;
+      } else {
+        cls |= (unsigned)c << (2 * k);
+        if (c == 1) lo0 = key_max(lo0, key_lo(key, err));
+        if (c == 2) lo1 = key_max(lo1, key_lo(key, err));
+      }
+    }
+  }
+  // pass 2 (rare): exact classification of the undecided points
+  if (und) {
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      if (!((und >> k) & 1u)) continue;
+      const int c = classify_exact(G, px[k], py[k]);
+      cls |= (unsigned)c << (2 * k);
+      if (c != 0) {
+        K key, err;
+        if (c == 1) line_key_k(l1, G.ax, G.ay, G.rx, G.ry, px[k], py[k], key, err);
+        else line_key_k(l2, G.rx, G.ry, G.bx, G.by, px[k], py[k], key, err);
+        if (c == 1) lo0 = key_max(lo0, key_lo(key, err));
+        else lo1 = key_max(lo1, key_lo(key, err));
+      }
+    }
+  }
+  // pass 3: this thread's exact farthest point per child among the points
+  // whose upper bound reaches the thread's best lower bound
+  CandT<K> b0 = cand_none<K>(), b1 = cand_none<K>();
+#pragma unroll
+  for (int k = 0; k < PPT; k++) {
+    const unsigned c = (cls >> (2 * k)) & 3u;
+    if (c == 0u) continue;
+    K key, err;
+    if (c == 1u) line_key_k(l1, G.ax, G.ay, G.rx, G.ry, px[k], py[k], key, err);
+    else line_key_k(l2, G.rx, G.ry, G.bx, G.by, px[k], py[k], key, err);
+    if (key_hi(key, err) < (c == 1u ? lo0 : lo1)) continue;
+    if (c == 1u) take_best(b0, G.ax, G.ay, G.rx, G.ry, px[k], py[k], pi[k], key, err);
+    else take_best(b1, G.rx, G.ry, G.bx, G.by, px[k], py[k], pi[k], key, err);
+  }
+#pragma unroll
+  for (int k = 0; k < PPT; k++) {
+    const unsigned c = (cls >> (2 * k)) & 3u;
+    const unsigned mL = __ballot_sync(kFull, c == 1u), mR = __ballot_sync(kFull, c == 2u);
+    if (lane == 0) {
+      sm.cnt[0][k * W + warp] = __popc(mL);
+      sm.cnt[1][k * W + warp] = __popc(mR);
+    }
+  }
+  __syncthreads();
+
+  // B: warp 0 scans the (round, warp) counts in round-major order, so a
+  // survivor's rank is its position among its child's survivors in the
+  // original point order
+  if (warp == 0) {
+#pragma unroll
+    for (int ch = 0; ch < 2; ch++) {
+      int v[PER];
+      int sum = 0;
+#pragma unroll
+      for (int q = 0; q < PER; q++) { v[q] = sm.cnt[ch][lane * PER + q]; sum += v[q]; }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < kWarp; o <<= 1) {
+        const int n = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += n;
+      }
+      int run = incl - sum;
+#pragma unroll
+      for (int q = 0; q < PER; q++) { sm.cnt[ch][lane * PER + q] = run; run += v[q]; }
+      if (lane == 31) sm.tot[ch] = incl;
+    }
+  }
+  __syncthreads();
+
+  // C: scatter survivors into the stage; reduce the argmax over the warp
+  {
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      const unsigned c = (cls >> (2 * k)) & 3u;
+      const unsigned mL = __ballot_sync(kFull, c == 1u), mR = __ballot_sync(kFull, c == 2u);
+      int pos = -1;
+      if (c == 1u) pos = sm.cnt[0][k * W + warp] + __popc(mL & lt);
+      else if (c == 2u) pos = TILE - 1 - (sm.cnt[1][k * W + warp] + __popc(mR & lt));
+      if (pos >= 0) { stx[pos] = px[k]; sty[pos] = py[k]; sti[pos] = pi[k]; }
+    }
+  }
+  if (__any_sync(kFull, b0.idx >= 0)) b0 = warp_best(G.ax, G.ay, G.rx, G.ry, b0);
+  if (__any_sync(kFull, b1.idx >= 0)) b1 = warp_best(G.rx, G.ry, G.bx, G.by, b1);
+  if (lane == 0) { sm.wc[0][warp] = to_double(b0); sm.wc[1][warp] = to_double(b1); }
+  __syncthreads();
+
+  // D: warp 0 finds the tile's offsets (look-back); warp 1 reduces the
+  // per-warp winners into the tile's candidates
+  const int tot0 = sm.tot[0], tot1 = sm.tot[1];
+  if (warp == 0) {
+    long long eL, eR;
+    const bool ok = lookback(w, par, t, S.tile_base, (unsigned long long)tot0, (unsigned long long)tot1, eL, eR, lane);
+    if (lane == 0) {
+      sm.excl[0] = ok ? (int)eL : -1;
+      sm.excl[1] = ok ? (int)eR : -1;
+    }
+  } else if (warp == 1) {
+    CandT<double> c0 = cand_none<double>(), c1 = cand_none<double>();
+    if (lane < W) { c0 = sm.wc[0][lane]; c1 = sm.wc[1][lane]; }
+    c0 = warp_best(G.ax, G.ay, G.rx, G.ry, c0);
+    c1 = warp_best(G.rx, G.ry, G.bx, G.by, c1);
+    if (lane == 0) {
+      TileCand tc;
+      tc.idx[0] = c0.idx; tc.lo[0] = c0.lo; tc.hi[0] = c0.hi;
+      tc.idx[1] = c1.idx; tc.lo[1] = c1.lo; tc.hi[1] = c1.hi;
+      w.cand[par][t] = tc;
+    }
+  }
+  __syncthreads();
+
+  // E: contiguous copy-out: left child forward from S.off + eL, right child
+  // (stored reversed at the stage's end) backward from the segment end
+  const int eL = sm.excl[0], eR = sm.excl[1];
+  if (eL >= 0 && eL + tot0 <= S.len && eR + tot1 <= S.len &&
+      VQ_OK_IDX(w, 9, (long long)S.off + S.len, 1, (long long)w.N + 1) && VQ_OK_IDX(w, 10, S.off, 0, w.N)) {
+    double* __restrict__ dx = w.bx[dstb];
+    double* __restrict__ dy = w.by[dstb];
+    int* __restrict__ di = w.bi[dstb];
+    const int l0 = S.off + eL;
+    for (int i = tid; i < tot0; i += T) {
+      __stcs(dx + l0 + i, stx[i]);
+      __stcs(dy + l0 + i, sty[i]);
+      __stcs(di + l0 + i, sti[i]);
+    }
+    const int r0 = S.off + S.len - eR - tot1;  // global position of stage index TILE - tot1
+    for (int i = tid; i < tot1; i += T) {
+      const int q = TILE - tot1 + i;
+      __stcs(dx + r0 + i, stx[q]);
+      __stcs(dy + r0 + i, sty[q]);
+      __stcs(di + r0 + i, sti[q]);
+    }
+  }
+}
+
+template <int PPT, bool SRC_INPUT>
+__global__ void __launch_bounds__(kK1Threads, 2) k_k1(Work w, int level) {
+  __shared__ K1Smem<PPT> sm;
+  extern __shared__ __align__(16) unsigned char k1_dyn[];
+  constexpr int TILE = kK1Threads * PPT;
+  double* stx = reinterpret_cast<double*>(k1_dyn);
+  double* sty = stx + TILE;
+  int* sti = reinterpret_cast<int*>(sty + TILE);
+  if (fatal(w)) return;
+  const int par = level & 1;
+  const int ntiles = min(*reinterpret_cast<volatile int*>(&w.ctrl->k1_tiles[par]), w.capT);
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) sm.tile = atomicAdd(&w.ctrl->k1_ticket, 1);
+    __syncthreads();
+    const int t = sm.tile;
+    if (t >= ntiles) break;
+    const int sid = w.tile_seg[par][t];
+    if (!VQ_OK_IDX(w, 20, sid, 0, w.capS)) break;
+    constexpr int SW = sizeof(SegRec) / 4, GW = sizeof(SegGeom) / 4;
+    if (tid < SW) reinterpret_cast<int*>(&sm.seg)[tid] = reinterpret_cast<const int*>(&w.segs[par][sid])[tid];
+    else if (tid < SW + GW)
+      reinterpret_cast<int*>(&sm.geom)[tid - SW] = reinterpret_cast<const int*>(&w.geom[par][sid])[tid - SW];
+    __syncthreads();
+    if (sm.seg.flags & kSegFast) k1_tile<PPT, SRC_INPUT, true>(w, level, t, sm, stx, sty, sti);
+    else k1_tile<PPT, SRC_INPUT, false>(w, level, t, sm, stx, sty, sti);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: per segment, cross-tile argmax, emission, children
+// ---------------------------------------------------------------------------
+
+__device__ CandT<double> reduce_tiles(const Work& w, int par, const SegRec& S, int ch, double ox, double oy,
+                                      double ex, double ey, int lane) {
+  const int end = S.tile_base + S.ntiles;
+  CandT<double> best = cand_none<double>();
+  for (int t = S.tile_base + lane; t < end; t += kWarp) {
+    const TileCand& c = w.cand[par][t];
+    const int idx = c.idx[ch];
+    if (idx < 0 || (best.idx >= 0 && c.hi[ch] < best.lo)) continue;
+    if (!VQ_OK_IDX(w, 11, idx, 0, w.N)) continue;
+    CandT<double> cc;
+    cc.idx = idx;
+    cc.lo = c.lo[ch];
+    cc.hi = c.hi[ch];
+    cc.x = w.x[idx];
+    cc.y = w.y[idx];
+    if (cand_beats(ox, oy, ex, ey, cc, best)) best = cc;
+  }
+  return warp_best(ox, oy, ex, ey, best);
+}
+
+__device__ void make_child(const Work& w, const SegRec& P, int a, int b, int r, int off, int len, int level,
+                           int buf, int lane) {
+  if (r < 0) {
+    if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
+    return;
+  }
+  if (len == 1) {  // a single point is its own farthest point: Alg. 1, |P| <= 1
+    if (lane == 0) emit(w, (long long)off + 1 + P.shift, r - P.set_off);
+    return;
+  }
+  SegRec C;
+  C.shift = P.shift;
+  C.off = off;
+  C.len = len;
+  C.a = a;
+  C.b = b;
+  C.r = r;
+  C.set_off = P.set_off;
+  C.level = level;
+  C.tile_base = 0;
+  C.ntiles = 0;
+  C.flags = (P.flags & kSegFast) | (buf ? kSegSrcBuf1 : 0);
+  if (len <= w.small_max) {
+    if (lane == 0) push_k3(w, C);
+  } else {
+    push_k1_warp(w, (level & 1), C, lane);
+  }
+}
+
+__global__ void k_k2(Work w, int level) {
+  if (fatal(w)) return;
+  const int par = level & 1, dstb = level & 1;
+  const int nseg = min(*reinterpret_cast<volatile int*>(&w.ctrl->k1_segs[par]), w.capS);
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int s = gw; s < nseg; s += nw) {
+    const SegRec S = w.segs[par][s];
+    const SegGeom& G = w.geom[par][s];
+    const double ax = G.ax, ay = G.ay, rx = G.rx, ry = G.ry, bx = G.bx, by = G.by;
+    const unsigned long long last = ld_volatile_u64(&w.status[par][S.tile_base + S.ntiles - 1]);
+    if ((last & kStFlagMask) != kStInc) {
+      if (lane == 0) atomicOr(&w.ctrl->err, kErrTimeout);
+      continue;
+    }
+    const int nL = (int)((last >> 31) & kCnt31), nR = (int)(last & kCnt31);
+    const CandT<double> bl = reduce_tiles(w, par, S, 0, ax, ay, rx, ry, lane);
+    const CandT<double> br = reduce_tiles(w, par, S, 1, rx, ry, bx, by, lane);
+    if (lane == 0) {
+      emit(w, (long long)S.off + nL + 1 + S.shift, S.r - S.set_off);
+      add_stats(w, S.level, S.len, nL + nR);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&w.ctrl->k1_read), (unsigned long long)S.len);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&w.ctrl->k1_kept), (unsigned long long)(nL + nR));
+    }
+    if (nL > 0) make_child(w, S, S.a, S.r, bl.idx, S.off, nL, S.level + 1, dstb, lane);
+    if (nR > 0) make_child(w, S, S.r, S.b, br.idx, S.off + S.len - nR, nR, S.level + 1, dstb, lane);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: small segments, one warp each, finished in shared memory
+// ---------------------------------------------------------------------------
+
+struct Frame {
+  int lo, hi;   // range in the warp's permutation buffer
+  int a, b, r;  // global indices; r < 0 until computed
+  int buf;
+  int depth;
+};
+
+template <bool FAST>
+__device__ int small_argmax(const double* X, const double* Y, const int* I, const unsigned short* P, int lo,
+                            int hi, double ox, double oy, double ex, double ey, int lane) {
+  typedef typename KeyOf<FAST>::T K;
+  LineF L;
+  if (FAST) L = make_line(ox, oy, ex, ey);
+  CandT<K> best = cand_none<K>();
+  for (int l = lo + lane; l < hi; l += kWarp) {
+    const int u = P[l];
+    K key, err;
+    line_key_k(L, ox, oy, ex, ey, X[u], Y[u], key, err);
+    take_best(best, ox, oy, ex, ey, X[u], Y[u], I[u], key, err);
+  }
+  best = warp_best(ox, oy, ex, ey, best);
+  return best.idx;
+}
+
+__device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y, int* I, unsigned short* P0,
+                            unsigned short* P1, Frame* stk, int lane) {
+  const bool fast = (S.flags & kSegFast) != 0;
+  const unsigned lt = lanemask_lt();
+  int top = 0;
+  if (lane == 0) {
+    Frame f;
+    f.lo = 0; f.hi = S.len; f.a = S.a; f.b = S.b; f.r = S.r; f.buf = 0; f.depth = 0;
+    stk[0] = f;
+  }
+  top = 1;
+  __syncwarp();
+  while (top > 0) {
+    top--;
+    const Frame f = stk[top];
+    __syncwarp();
+    if (!VQ_OK_IDX(w, 12, f.a, 0, w.N) || !VQ_OK_IDX(w, 13, f.b, 0, w.N) ||
+        !VQ_OK_IDX(w, 14, f.hi, f.lo + 1, S.len + 1) || !VQ_OK_IDX(w, 15, f.lo, 0, S.len))
+      return;
+    unsigned short* Pin = f.buf ? P1 : P0;
+    unsigned short* Pout = f.buf ? P0 : P1;
+    const double ax = w.x[f.a], ay = w.y[f.a], bx = w.x[f.b], by = w.y[f.b];
+    int r = f.r;
+    if (r < 0)
+      r = fast ? small_argmax<true>(X, Y, I, Pin, f.lo, f.hi, ax, ay, bx, by, lane)
+               : small_argmax<false>(X, Y, I, Pin, f.lo, f.hi, ax, ay, bx, by, lane);
+    if (r < 0) {
+      if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
+      return;
+    }
+    if (!VQ_OK_IDX(w, 16, r, 0, w.N)) return;
+    const double rx = w.x[r], ry = w.y[r];
+    SegGeom G;
+    G.ax = ax; G.ay = ay; G.bx = bx; G.by = by; G.rx = rx; G.ry = ry;
+    LineF l1, l2;
+    if (fast) { l1 = make_line(ax, ay, rx, ry); l2 = make_line(rx, ry, bx, by); }
+    int nL = 0, nR = 0;
+    for (int base = f.lo; base < f.hi; base += kWarp) {
+      const int l = base + lane;
+      int c = 0;
+      unsigned short u = 0;
+      if (l < f.hi) {
+        u = Pin[l];
+        if (fast) { float k, e; c = classify_fast(G, l1, l2, X[u], Y[u], k, e); }
+        else { double k, e; c = classify_slow(G, X[u], Y[u], k, e); }
+      }
+      const unsigned mL = __ballot_sync(kFull, c == 1), mR = __ballot_sync(kFull, c == 2);
+      if (c == 1) Pout[f.lo + nL + __popc(mL & lt)] = u;
+      if (c == 2) Pout[f.hi - 1 - (nR + __popc(mR & lt))] = u;
+      nL += __popc(mL);
+      nR += __popc(mR);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      emit(w, (long long)S.off + f.lo + nL + 1 + S.shift, r - S.set_off);
+      add_stats(w, S.level + f.depth, f.hi - f.lo, nL + nR);
+    }
+    // children: left [lo, lo+nL) on a->r, right [hi-nR, hi) on r->b
+    Frame cl, cr;
+    cl.lo = f.lo; cl.hi = f.lo + nL; cl.a = f.a; cl.b = r; cl.r = -1; cl.buf = f.buf ^ 1; cl.depth = f.depth + 1;
+    cr.lo = f.hi - nR; cr.hi = f.hi; cr.a = r; cr.b = f.b; cr.r = -1; cr.buf = f.buf ^ 1; cr.depth = f.depth + 1;
+    if (lane == 0) {
+      if (nL == 1) { const int u = Pout[cl.lo]; emit(w, (long long)S.off + cl.lo + 1 + S.shift, I[u] - S.set_off); }
+      if (nR == 1) { const int u = Pout[cr.lo]; emit(w, (long long)S.off + cr.lo + 1 + S.shift, I[u] - S.set_off); }
+    }
+    const bool pl = nL >= 2, pr = nR >= 2;
+    const int need = (pl ? 1 : 0) + (pr ? 1 : 0);
+    if (top + need > kK3Stack) {
+      if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
+      return;
+    }
+    if (lane == 0) {
+      // larger child first so the smaller one is processed next (stack depth <= log2 n + 1)
+      if (pl && pr) {
+        if (nL >= nR) { stk[top] = cl; stk[top + 1] = cr; }
+        else { stk[top] = cr; stk[top + 1] = cl; }
+      } else if (pl) {
+        stk[top] = cl;
+      } else if (pr) {
+        stk[top] = cr;
+      }
+    }
+    top += need;
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kK3Warps * kWarp) k_k3(Work w) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (fatal(w)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t per = (size_t)kK3Cap * 24 + sizeof(Frame) * kK3Stack;
+  unsigned char* base = smem + per * warp;
+  double* X = reinterpret_cast<double*>(base);
+  double* Y = X + kK3Cap;
+  int* I = reinterpret_cast<int*>(Y + kK3Cap);
+  unsigned short* P0 = reinterpret_cast<unsigned short*>(I + kK3Cap);
+  unsigned short* P1 = P0 + kK3Cap;
+  Frame* stk = reinterpret_cast<Frame*>(P1 + kK3Cap);
+  const int nq = min(*reinterpret_cast<volatile int*>(&w.ctrl->k3_count), w.capQ);
+  for (int e = blockIdx.x * kK3Warps + warp; e < nq; e += gridDim.x * kK3Warps) {
+    const SegRec S = w.k3q[e];
+    if (!VQ_OK_IDX(w, 17, (long long)S.off + S.len, 1, (long long)w.N + 1) || !VQ_OK_IDX(w, 18, S.r, 0, w.N))
+      continue;
+    if (S.len > kK3Cap) {
+      if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
+      continue;
+    }
+    const double* sx;
+    const double* sy;
+    const int* si = nullptr;
+    if (S.flags & kSegSrcInput) {
+      sx = w.x; sy = w.y;
+    } else {
+      const int b = (S.flags & kSegSrcBuf1) ? 1 : 0;
+      sx = w.bx[b]; sy = w.by[b]; si = w.bi[b];
+    }
+    for (int l = lane; l < S.len; l += kWarp) {
+      X[l] = sx[S.off + l];
+      Y[l] = sy[S.off + l];
+      I[l] = si ? si[S.off + l] : S.off + l;
+      P0[l] = (unsigned short)l;
+    }
+    __syncwarp();
+    small_solve(w, S, X, Y, I, P0, P1, stk, lane);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: order the emitted vertices by key (bitmap compaction)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int block_excl_scan_256(int v, int* sh, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < kWarp; o <<= 1) {
+    const int n = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int s = lane < 8 ? sh[lane] : 0;
+    int si = s;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int n = __shfl_up_sync(kFull, si, o);
+      if (lane >= o) si += n;
+    }
+    if (lane < 8) sh[8 + lane] = si - s;
+    if (lane == 7) sh[16] = si;
+  }
+  __syncthreads();
+  const int r = sh[8 + warp] + incl - v;
+  total = sh[16];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_k4_count(const unsigned* bm, long long nwords, long long* sums,
+                                                  long long nb) {
+  __shared__ int sh[24];
+  if (blockIdx.x == 0 && threadIdx.x == 0) sums[nb] = 0;  // becomes the total after the scan
+  const long long w0 = (long long)blockIdx.x * kK4Words + threadIdx.x * 4;
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    if (w0 + q < nwords) c += __popc(bm[w0 + q]);
+  int total;
+  block_excl_scan_256(c, sh, total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(256) k_k4_write(const unsigned* bm, long long nwords, const long long* sums,
+                                                  const int* slot, int* out, long long cap, Ctrl* ctrl) {
+  __shared__ int sh[24];
+  const long long w0 = (long long)blockIdx.x * kK4Words + threadIdx.x * 4;
+  unsigned v[4];
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    v[q] = (w0 + q < nwords) ? bm[w0 + q] : 0u;
+    c += __popc(v[q]);
+  }
+  int total;
+  const int pre = block_excl_scan_256(c, sh, total);
+  long long pos = sums[blockIdx.x] + pre;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    unsigned m = v[q];
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+#ifdef VQ_CHECKED
+      if (pos >= cap) {
+        if (atomicCAS(&ctrl->dbg_site, 0, 19) == 0) ctrl->dbg_val = pos;
+        atomicOr(&ctrl->err, kErrInternal);
+        return;
+      }
+#endif
+      out[pos++] = slot[(w0 + q) * 32 + b];
+    }
+  }
+}
+
+__device__ __forceinline__ long long key_rank(const unsigned* bm, long long nwords, const long long* sums,
+                                              long long key) {
+  const long long word = key >> 5;
+  const long long blk = word / kK4Words;
+  long long r = sums[blk];
+  for (long long q = blk * kK4Words; q < word && q < nwords; q++) r += __popc(bm[q]);
+  if (word < nwords) r += __popc(bm[word] & ((1u << (unsigned)(key & 31)) - 1u));
+  return r;
+}
+
+__global__ void k_k4_offsets(Work w, const long long* sums, long long* hull_offsets, long long* total) {
+  const long long nwords = (w.nkeys + 31) >> 5;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > w.nsets) return;
+  const long long key = s < w.nsets ? (long long)w.sets[s].off + w.sets[s].shift : w.nkeys;
+  const long long r = key_rank(w.bitmap, nwords, sums, key);
+  if (hull_offsets) hull_offsets[s] = r;
+  if (s == w.nsets && total) *total = r;
+}
+
+// ---------------------------------------------------------------------------
+// generic exclusive scan (in place), 2048 items per block, recursive
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_scan_block(T* data, long long n, T* sums) {
+  __shared__ T sh[24];
+  const long long b0 = (long long)blockIdx.x * 2048 + threadIdx.x * 8;
+  T v[8];
+  T s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    v[q] = (b0 + q < n) ? data[b0 + q] : (T)0;
+    s += v[q];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T incl = s;
+#pragma unroll
+  for (int o = 1; o < kWarp; o <<= 1) {
+    const T m = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += m;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T run = 0;
+    for (int q = 0; q < 8; q++) { const T t = sh[q]; sh[8 + q] = run; run += t; }
+    sh[16] = run;
+  }
+  __syncthreads();
+  T run = sh[8 + warp] + incl - s;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    if (b0 + q < n) data[b0 + q] = run;
+    run += v[q];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = sh[16];
+}
+
+template <typename T>
+__global__ void k_scan_add(T* data, long long n, const T* sums) {
+  const long long b0 = (long long)blockIdx.x * 2048;
+  const T add = sums[blockIdx.x];
+  for (int q = threadIdx.x; q < 2048; q += blockDim.x)
+    if (b0 + q < n) data[b0 + q] += add;
+}
+
+template <typename T>
+static cudaError_t scan_rec(T* data, long long n, T* tmp, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long nb = (n + 2047) / 2048;
+  count_launch();
+  k_scan_block<T><<<(unsigned)nb, 256, 0, st>>>(data, n, tmp);
+  if (nb > 1) {
+    cudaError_t e = scan_rec<T>(tmp, nb, tmp + nb, st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_scan_add<T><<<(unsigned)nb, 256, 0, st>>>(data, n, tmp);
+  }
+  return cudaGetLastError();
+}
+
+long long scan_tmp_elems(long long n) {
+  long long t = 0;
+  while (n > 1) {
+    n = (n + 2047) / 2048;
+    t += n;
+  }
+  return t + 8;
+}
+
+cudaError_t scan_exclusive_i32(int* data, long long n, int* tmp, cudaStream_t st) {
+  return scan_rec<int>(data, n, tmp, st);
+}
+cudaError_t scan_exclusive_i64(long long* data, long long n, long long* tmp, cudaStream_t st) {
+  return scan_rec<long long>(data, n, tmp, st);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+
+cudaError_t launch_seed(const Work& w, cudaStream_t st) {
+  const int blocks = (w.nsets + 255) / 256;
+  count_launch();
+  k_seed<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_k0(const Work& w, int grid, cudaStream_t st) {
+  count_launch();
+  k_k0<<<grid, kK0Threads, 0, st>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st) {
+  const long long warps = w.nsets;
+  long long blocks = (warps * 32 + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launch();
+  k_k0_finalize<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st) {
+  count_launch();
+  k_prologue<<<1, 1, 0, st>>>(w, level);
+  return cudaGetLastError();
+}
+
+template <int PPT>
+static cudaError_t k1_attrs() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (done[dev]) return cudaSuccess;
+  const int bytes = (int)K1Stage<PPT>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_k1<PPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_k1<PPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
+template <int PPT>
+static cudaError_t launch_k1_ppt(const Work& w, int level, int grid, cudaStream_t st) {
+  cudaError_t e = k1_attrs<PPT>();
+  if (e != cudaSuccess) return e;
+  const size_t bytes = K1Stage<PPT>::bytes;
+  count_launch();
+  if (level == 0) k_k1<PPT, true><<<grid, kK1Threads, bytes, st>>>(w, level);
+  else k_k1<PPT, false><<<grid, kK1Threads, bytes, st>>>(w, level);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st) {
+  switch (ppt) {
+    case 4: return launch_k1_ppt<4>(w, level, grid, st);
+    case 8: return launch_k1_ppt<8>(w, level, grid, st);
+    case 16: return launch_k1_ppt<16>(w, level, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int PPT>
+static int k1_occ() {
+  if (k1_attrs<PPT>() != cudaSuccess) return 1;
+  int n = 0, n0 = 0;
+  const size_t bytes = K1Stage<PPT>::bytes;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_k1<PPT, false>, kK1Threads, bytes) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_k1<PPT, true>, kK1Threads, bytes) != cudaSuccess) return 1;
+  n = n0 < n ? n0 : n;
+  return n > 0 ? n : 1;
+}
+
+int k1_blocks_per_sm(int ppt) {
+  switch (ppt) {
+    case 4: return k1_occ<4>();
+    case 8: return k1_occ<8>();
+    case 16: return k1_occ<16>();
+    default: return 1;
+  }
+}
+
+cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st) {
+  count_launch();
+  k_k2<<<grid, 256, 0, st>>>(w, level);
+  return cudaGetLastError();
+}
+
+int k3_smem_bytes() { return (int)(((size_t)kK3Cap * 24 + sizeof(Frame) * kK3Stack) * kK3Warps); }
+
+cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st) {
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_k3, cudaFuncAttributeMaxDynamicSharedMemorySize, k3_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  count_launch();
+  k_k3<<<grid, kK3Warps * kWarp, k3_smem_bytes(), st>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long long* total, long long* tmp,
+                         cudaStream_t st) {
+  const long long nwords = (w.nkeys + 31) >> 5;
+  const long long nb = (nwords + kK4Words - 1) / kK4Words;
+  long long* sums = tmp;  // nb + 1 entries: block prefixes, then the total
+  count_launch();
+  k_k4_count<<<(unsigned)nb, 256, 0, st>>>(w.bitmap, nwords, sums, nb);
+  cudaError_t e = scan_exclusive_i64(sums, nb + 1, tmp + nb + 1, st);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k_k4_write<<<(unsigned)nb, 256, 0, st>>>(w.bitmap, nwords, sums, w.slot, out, (long long)w.N, w.ctrl);
+  const int blocks = (w.nsets + 1 + 255) / 256;
+  count_launch();
+  k_k4_offsets<<<blocks, 256, 0, st>>>(w, sums, hull_offsets, total);
+  return cudaGetLastError();
+}
+
+}  // namespace vq

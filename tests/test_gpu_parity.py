@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Hull index lists are compared element by element (bit-exact), and the
+per-level partition counters are compared with the oracle's, which use the
+same tie rule.  Sizes span several partition tiles, ragged tails and every
+level kind (level 0, big-segment levels, the shared-memory finisher).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2510_09417_gb300 as v
+    v.load()
+    return v
+
+
+@pytest.fixture(autouse=True)
+def _default_config(vq):
+    cfg = vq.vq_get_config()
+    yield
+    vq.vq_set_config(cfg)
+
+
+def gpu_hull(vq, x, y):
+    xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+    yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float64)).cuda()
+    return vq.vq_hull2d(xd, yd).cpu().numpy()
+
+
+def check(vq, x, y, stats=False):
+    got = gpu_hull(vq, x, y)
+    if stats:
+        want, st = oracle.hull(x, y, stats=True)
+    else:
+        want = oracle.hull(x, y)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    assert np.array_equal(got, want)
+    if stats:
+        gs = vq.vq_last_stats()
+        L = st["levels"]
+        assert gs["levels"] == L
+        assert gs["read"] == st["read"]
+        assert gs["written"] == st["written"]
+        assert gs["segments"] == st["segments"]
+    return got
+
+
+@pytest.mark.parametrize("dist", synth.DISTRIBUTIONS)
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 1000, 5000, 70_001])
+def test_distributions(vq, dist, n):
+    x, y = synth.points(dist, n, 1000 + n)
+    check(vq, x, y, stats=True)
+
+
+@pytest.mark.parametrize("small_max", [2, 64, 1024])
+@pytest.mark.parametrize("ppt", [4, 8, 16])
+def test_tilings(vq, small_max, ppt):
+    """Every tile size and small-segment threshold gives the same hull and
+    the same per-level counts."""
+    vq.vq_set_config(points_per_thread=ppt, small_max=small_max)
+    for dist, n in (("disk", 300_000), ("circle", 50_000), ("square", 123_457)):
+        x, y = synth.points(dist, n, 7)
+        check(vq, x, y, stats=True)
+
+
+def test_degenerate(vq):
+    rng = np.random.default_rng(4)
+    cases = []
+    cases.append((np.array([]), np.array([])))
+    cases.append((np.full(10_000, 3.0), np.full(10_000, -2.0)))       # coincident
+    t = rng.permutation(50_000).astype(float)
+    cases.append((t, 3 * t - 7))                                       # collinear
+    cases.append((np.zeros(20_000), rng.random(20_000)))              # vertical line
+    g = rng.integers(0, 50, (2, 200_000)).astype(float)
+    cases.append((g[0], g[1]))                                         # grid with duplicates
+    k = 6
+    gx, gy = np.meshgrid(np.arange(k + 1.0), np.arange(k + 1.0))
+    cases.append((np.tile(gx.ravel(), 500), np.tile(gy.ravel(), 500)))  # lattice, many copies
+    par = rng.permutation(np.arange(-40_000, 40_000, dtype=float))
+    cases.append((par, par * par))                                     # parabola: all vertices
+    x, y = synth.points("disk", 100_000, 5)
+    cases.append((np.concatenate([x, x]), np.concatenate([y, y])))     # every point twice
+    cases.append((x * 2.0 ** 200, y * 2.0 ** -200))                    # outside the FP32 tier's range
+    cases.append((x * 2.0 ** -300, y * 2.0 ** -300))                   # tiny magnitudes
+    for x, y in cases:
+        check(vq, x, y)
+
+
+def test_config1_square_1e6(vq):
+    x, y = synth.workload("square", 1_000_000)
+    check(vq, x, y, stats=True)
+
+
+@pytest.mark.parametrize("dist", ["square", "disk", "kuzmin", "circle"])
+def test_full_size_1e8(vq, dist):
+    """The 1e8-point workloads: complete verification of the hull (unique by
+    its invariants) at full size, plus exact equality with the oracle where
+    it finishes in seconds."""
+    x, y = synth.workload(dist, 100_000_000)
+    got = gpu_hull(vq, x, y)
+    code, bad = oracle.verify(x, y, got)
+    assert code == 0, (oracle.VERIFY_CODES.get(code), bad)
+    if dist in ("square", "kuzmin"):
+        assert np.array_equal(got, oracle.hull(x, y))
+
+
+def test_nonfinite(vq):
+    x, y = synth.points("disk", 10_000, 1)
+    x[1234] = np.nan
+    with pytest.raises(vq.VQError) as e:
+        gpu_hull(vq, x, y)
+    assert e.value.status == -2
+
+
+def test_batched_matches_single(vq):
+    x, y, offs, dists = synth.batched_sets(nsets=300, lo=1, hi=200_000, seed=9)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    od = torch.from_numpy(offs).cuda()
+    hi, ho = vq.vq_hull2d_batched(xd, yd, od)
+    hi, ho = hi.cpu().numpy(), ho.cpu().numpy()
+    for s in range(300):
+        a, b = offs[s], offs[s + 1]
+        want = oracle.hull(x[a:b], y[a:b])
+        got = hi[ho[s]:ho[s + 1]]
+        assert np.array_equal(got, want), s
+
+
+def test_batched_empty_sets(vq):
+    x, y = synth.points("square", 1000, 2)
+    offs = np.array([0, 0, 10, 10, 1000, 1000], dtype=np.int64)
+    hi, ho = vq.vq_hull2d_batched(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(),
+                                  torch.from_numpy(offs).cuda())
+    hi, ho = hi.cpu().numpy(), ho.cpu().numpy()
+    for s in range(5):
+        a, b = offs[s], offs[s + 1]
+        assert np.array_equal(hi[ho[s]:ho[s + 1]], oracle.hull(x[a:b], y[a:b]))
+
+
+def test_host_entry_point(vq):
+    x, y = synth.points("kuzmin", 200_000, 3)
+    got = vq.vq_hull2d_host(x, y)
+    assert np.array_equal(got, oracle.hull(x, y))
+
+
+def test_lookback_timeout_is_reported(vq):
+    """A tile that never publishes its look-back status makes its successors'
+    bounded waits expire; the call reports VQ_ERR_TIMEOUT and the device
+    stays usable."""
+    x, y = synth.points("square", 400_000, 3)
+    vq.vq_set_config(debug_drop_tile=2, timeout_ns=20_000_000)
+    with pytest.raises(vq.VQError) as e:
+        gpu_hull(vq, x, y)
+    assert e.value.status == -6
+    vq.vq_set_config(debug_drop_tile=-1, timeout_ns=2_000_000_000)
+    check(vq, x, y)
+
+
+@pytest.mark.parametrize("ppt", [4, 8, 16])
+def test_all_points_on_hull(vq, ppt):
+    """Point sets where every point is a hull vertex (circle samples of
+    1e5-2e5 points): the exact tiers decide most classifications and
+    farthest points at every level, in big segments of one to a few tiles."""
+    vq.vq_set_config(points_per_thread=ppt)
+    # set 150 of the 300-set batched case (seed 9): 185,768 circle points
+    x, y = synth.points("circle", 185_768, (9 << 20) + 150)
+    check(vq, x, y, stats=True)
+    for n, seed in ((100_000, 1), (150_001, 2), (200_000, 3)):
+        x, y = synth.points("circle", n, seed)
+        check(vq, x, y, stats=True)
