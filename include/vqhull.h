@@ -104,6 +104,30 @@ vq_status vq_hull2d_batched(const double* x, const double* y, const int64_t* off
 vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, int32_t* hull_idx_host,
                          int64_t* h, void* stream);
 
+/*
+ * vq_hull2d for callers that cannot allocate.  The paper has no counterpart:
+ * this entry point exists for code that must not trigger a device or host
+ * allocation from inside a library call -- work recorded while a CUDA graph
+ * is being captured, hosts that forbid allocation after start-up, and
+ * processes whose device memory is handed out by their own pool allocator.
+ * It runs the same kernels as vq_hull2d, but its whole workspace is one
+ * fixed 64 MiB array of device memory that is part of this library; every
+ * GPU that loads the library reserves it until the process exits.  The call
+ * makes no cudaMalloc, cudaMallocHost, cudaFree or other allocating call.
+ *   x, y, hull_idx, h, stream   as for vq_hull2d (hull_idx: room for n)
+ *   n                           0 <= n <= 1,048,576; larger n returns
+ *                               VQ_ERR_TOO_LARGE without touching the device
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  All calls on a device share the array,
+ * which keeps the previous call's contents (each call clears what it needs
+ * zeroed); calls that overlap on the GPU would race on it.  This function
+ * therefore takes a process-wide lock and waits for `stream` before it
+ * returns, so calls made through it never overlap.
+ */
+vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t n, int32_t* hull_idx, int64_t* h,
+                            void* stream);
+
 /* Tuning knobs (process-wide; take effect on the next call). */
 typedef struct {
   int32_t points_per_thread; /* partition kernel: 4, 8 or 16 points per thread */

@@ -67,7 +67,7 @@ class ServerConfig(ctypes.Structure):
 
 
 SYMBOLS = (
-    "vq_status_string", "vq_version", "vq_hull2d", "vq_hull2d_batched", "vq_hull2d_host",
+    "vq_status_string", "vq_version", "vq_hull2d", "vq_hull2d_batched", "vq_hull2d_host", "vq_hull2d_noalloc",
     "vq_get_config", "vq_set_config", "vq_last_stats", "vq_profile_read", "vq_server_create", "vq_server_submit",
     "vq_server_poll", "vq_server_wait", "vq_server_stats", "vq_server_destroy",
 )
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
         lib.vq_hull2d_batched.restype = ctypes.c_int
         lib.vq_hull2d_host.argtypes = [vp, vp, i64, vp, i64p, vp]
         lib.vq_hull2d_host.restype = ctypes.c_int
+        lib.vq_hull2d_noalloc.argtypes = [vp, vp, i64, vp, i64p, vp]
+        lib.vq_hull2d_noalloc.restype = ctypes.c_int
         lib.vq_get_config.argtypes = [ctypes.POINTER(Config)]
         lib.vq_get_config.restype = ctypes.c_int
         lib.vq_set_config.argtypes = [ctypes.POINTER(Config)]
@@ -211,6 +213,23 @@ def vq_hull2d_host(x, y, hull_idx=None, stream=None):
     st = lib.vq_hull2d_host(xa.ctypes.data, ya.ctypes.data, n, out_ptr, ctypes.byref(h), _stream_ptr(stream))
     _check(st, "vq_hull2d_host")
     return out[: h.value]
+
+
+def vq_hull2d_noalloc(x: torch.Tensor, y: torch.Tensor, hull_idx: torch.Tensor, stream=None):
+    """vq_hull2d without any allocation inside the library (fixed scratch;
+    n <= 1,048,576).  The caller provides hull_idx (int32, room for n)."""
+    lib = load()
+    x, y = _dev_f64(x, "x"), _dev_f64(y, "y")
+    n = x.shape[0]
+    if y.shape[0] != n:
+        raise ValueError("x and y differ in length")
+    if hull_idx.dtype != torch.int32 or hull_idx.numel() < n or not hull_idx.is_cuda:
+        raise ValueError("hull_idx must be an int32 CUDA tensor with room for n indices")
+    h = ctypes.c_int64(0)
+    st = lib.vq_hull2d_noalloc(x.data_ptr(), y.data_ptr(), n, hull_idx.data_ptr(), ctypes.byref(h),
+                               _stream_ptr(stream))
+    _check(st, "vq_hull2d_noalloc")
+    return hull_idx[: h.value]
 
 
 def vq_get_config() -> Config:
