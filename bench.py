@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=30_000_000,
                     help="points per workload for the CPU-oracle baseline")
+    ap.add_argument("--ppt", type=int, default=0, help="tuning: points per lane of the partition kernel")
+    ap.add_argument("--small-max", type=int, default=0, help="tuning: small-segment threshold")
     return ap.parse_args()
 
 
@@ -196,6 +198,10 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     vq.load()
+    if args.ppt:
+        vq.vq_set_config(points_per_thread=args.ppt)
+    if args.small_max:
+        vq.vq_set_config(small_max=args.small_max)
     n = args.n
     if n == FULL_N:
         data = [synth.workload(d, n) for d in ("square", "disk")]
@@ -297,6 +303,8 @@ def main():
                        "parallelism": f"replicas x{ws}", "hull_sizes": hull_sizes},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
+            "tuning": {"points_per_lane": int(vq.vq_get_config().points_per_thread),
+                       "small_max": int(vq.vq_get_config().small_max)},
             "detail": {"profile": prof,
                        "paper_model_GBps": (8.0 * 2 * n * args.steps + k1_bytes) / (ms_max / 1e3) / 1e9},
         }

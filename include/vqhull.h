@@ -133,13 +133,16 @@ typedef struct {
   int32_t points_per_thread; /* partition kernel: 4, 8 or 16 points per thread */
   int32_t small_max;         /* segments of <= small_max points (2..1024) are
                                 finished by the shared-memory kernel          */
-  int32_t k1_blocks_per_sm;  /* partition blocks per SM; 0 = occupancy limit  */
+  int32_t k1_blocks_per_sm;  /* reserved (partition blocks are one per tile)  */
   int32_t profile;           /* 1: time every kernel with CUDA events (see
                                 vq_profile_read); 0: off                     */
   int64_t timeout_ns;        /* bound of every device-side wait              */
   int32_t debug_drop_tile;   /* testing: this partition tile never publishes
                                 its look-back status (-1 = off)              */
-  int32_t reserved1;
+  int32_t ordered;           /* 1: partition offsets by decoupled look-back
+                                (stable, run-to-run identical buffer layout);
+                                0 (default): one atomic per tile (faster; the
+                                hull is identical either way)               */
 } vq_config;
 
 vq_status vq_get_config(vq_config* cfg);

@@ -21,6 +21,7 @@ struct Config {
   int small_max = 1024;
   int k1_bps = 0;
   int profile = 0;
+  int ordered = 0;
   long long timeout_ns = 2000000000ll;
   int drop_tile = -1;
 };
@@ -153,7 +154,7 @@ static size_t layout(Work& w, char* base, long long N, int nsets, long long nkey
   w.capT0 = (int)(n / kK0Tile + nsets + 1);
   w.k0part = reinterpret_cast<K0Part*>(take(sizeof(K0Part) * w.capT0));
   w.small_max = cfg.small_max;
-  w.tile = kK1Threads * cfg.ppt;
+  w.tile = kK1Threads * cfg.ppt;  // partition block tile: 256 threads x ppt points
   w.capS = (int)(n / (cfg.small_max + 1) + 2);
   w.capT = (int)(n / w.tile + w.capS + 1);
   w.capQ = 2 * w.capS + nsets + 16;
@@ -162,7 +163,8 @@ static size_t layout(Work& w, char* base, long long N, int nsets, long long nkey
     w.geom[b] = reinterpret_cast<SegGeom*>(take(sizeof(SegGeom) * w.capS));
     w.tile_seg[b] = reinterpret_cast<int*>(take(sizeof(int) * w.capT));
     w.status[b] = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * w.capT));
-    w.cand[b] = reinterpret_cast<TileCand*>(take(sizeof(TileCand) * w.capT));
+    w.cand[b] = reinterpret_cast<TileRec*>(take(sizeof(TileRec) * w.capT));
+    w.sstate[b] = reinterpret_cast<SegState*>(take(sizeof(SegState) * w.capS));
   }
   w.k3q = reinterpret_cast<SegRec*>(take(sizeof(SegRec) * w.capQ));
   w.ctrl = reinterpret_cast<Ctrl*>(take(sizeof(Ctrl)));
@@ -212,12 +214,6 @@ static vq_status ctx_reserve(Ctx& c, size_t bytes) {
   return VQ_OK;
 }
 
-static int k1_bps(Ctx& c, const Config& cfg) {
-  if (cfg.k1_bps > 0) return cfg.k1_bps;
-  if (!c.bps_cache[cfg.ppt]) c.bps_cache[cfg.ppt] = k1_blocks_per_sm(cfg.ppt);
-  return c.bps_cache[cfg.ppt];
-}
-
 // The level loop shared by the single and batched entry points.
 static vq_status run(Ctx& c, const double* x, const double* y, const long long* offsets, long long n_single,
                      int nsets, long long N, int* out, long long* hull_offsets, long long* h_out,
@@ -241,6 +237,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   w.N = (int)N;
   w.timeout_ns = cfg.timeout_ns;
   w.drop_tile = cfg.drop_tile;
+  w.ordered = cfg.ordered;
   c.d_stats = w.stats;
 
   const long long launches0 = kernels_launched();
@@ -257,12 +254,14 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   VQ_CHECK(launch_k0_finalize(w, st));
   VQ_CHECK(tm.end());
 
-  const int bps = k1_bps(c, cfg);
   int level = 0;
   int levels_run = 0;
+  // one partition block per tile: level 0 uses the bound (one segment per
+  // point set), later levels the count the previous level produced
+  long long k1_grid = N / w.tile + nsets + 1;
   for (;; level++) {
     VQ_TIMED(tm, kKindOther, launch_prologue(w, level, st));
-    VQ_TIMED(tm, kKindK1, launch_k1(w, level, cfg.ppt, c.sms * bps, st));
+    if (k1_grid > 0) VQ_TIMED(tm, kKindK1, launch_k1(w, level, cfg.ppt, (int)k1_grid, st));
     c.prof.k1_launches++;
     VQ_TIMED(tm, kKindK2, launch_k2(w, level, c.sms * 8, st));
     VQ_TIMED(tm, kKindK3, launch_k3(w, c.sms * 2, st));
@@ -271,6 +270,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
     levels_run = level + 1;
     if (c.h_ctrl->err & kErrFatal) break;
     if (c.h_ctrl->k1_segs[(level + 1) & 1] == 0) break;
+    k1_grid = c.h_ctrl->k1_tiles[(level + 1) & 1];
     if (level > N + 1) {  // every level removes at least one point per segment
       c.h_ctrl->err |= kErrInternal;
       break;
@@ -423,6 +423,7 @@ vq_status vq_get_config(vq_config* cfg) {
   cfg->profile = c.profile;
   cfg->timeout_ns = c.timeout_ns;
   cfg->debug_drop_tile = c.drop_tile;
+  cfg->ordered = c.ordered;
   return VQ_OK;
 }
 
@@ -440,6 +441,7 @@ vq_status vq_set_config(const vq_config* cfg) {
   g_cfg.profile = cfg->profile ? 1 : 0;
   g_cfg.timeout_ns = cfg->timeout_ns;
   g_cfg.drop_tile = cfg->debug_drop_tile;
+  g_cfg.ordered = cfg->ordered ? 1 : 0;
   return VQ_OK;
 }
 

@@ -86,7 +86,7 @@ struct SegRec {
 // Per-segment constants of the FP32 tier and the exact endpoints.
 // Line 1 is a->r (left child), line 2 is r->b (right child).
 struct SegGeom {
-  double ax, ay, rx, ry, bx, by;
+  double ax, ay, rx, ry, bx, by;  // line 1 = {ax, ay, rx, ry}, line 2 = {rx, ry, bx, by}
   float o1x, o1y, o2x, o2y;  // origins: truncated a and r (same conversion as points)
   float d1x, d1y, d2x, d2y;  // rounded r-a and b-r
   float k1, c1, k2, c2;      // error bound: E = k*(|ux~|+|uy~|) + c + 2^-22 |d~|
@@ -101,12 +101,54 @@ struct SetRec {
   int pad;
 };
 
-// Tile winners of the fused argmax, for the left (0) and right (1) child.
-struct TileCand {
-  int idx[2];
-  double lo[2];  // bounds of the winner's orient w.r.t. the child's line
-  double hi[2];
+// A farthest-point candidate published through the look-back: the point,
+// bounds lo <= orient(child line, point) <= hi, and its index (-1: none).
+struct BestRec {
+  double x, y;
+  double lo, hi;
+  int idx;
+  int pad;
 };
+
+// Per partition tile and child (0 = left, 1 = right): the tile's own
+// farthest point (written before its aggregate status) and the running
+// farthest point over the segment's tiles up to this one (written before
+// its inclusive status).  The last tile's inclusive records are the
+// children's farthest points.
+struct TileRec {
+  BestRec own[2];
+  BestRec incl[2];
+};
+
+// Per big segment and level: output cursors and farthest-point candidates.
+// cursor packs the children's counts (left << 32 | right); tiles add their
+// counts atomically and get their output offsets back.  lomax[c] is the
+// largest lower bound of child c's key seen so far (order-preserving u64 of
+// an FP64 value); a tile whose best upper bound reaches it adds its index to
+// cand[c].  The child's farthest point is the exact best among the listed
+// tiles' own records with hi >= the final lomax; more than kMaxCand entries
+// (ncand) fall back to scanning every tile's record.
+constexpr int kMaxCand = 32;
+struct SegState {
+  unsigned long long cursor;
+  unsigned long long lomax[2];
+  int ncand[2];
+  int cand[2][kMaxCand];
+};
+
+__host__ __device__ inline unsigned long long dkey(double v) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &v, 8);
+#endif
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ inline double dkey_inv(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
 
 struct K0Part {
   long long minx, miny, maxx, maxy;  // ordered-integer keys
@@ -137,6 +179,16 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 
 __device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
   *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+
+// release store / acquire load at GPU scope (look-back status words)
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
 // Doubles as signed integers with the same order; -0 and +0 map to 0.
@@ -322,14 +374,15 @@ static __device__ __forceinline__ bool beats_exact(double ox, double oy, double 
   return ui < vi;
 }
 
+// L points at the line's endpoints {ox, oy, ex, ey} (read only when the
+// bounds overlap, so the hot paths keep no FP64 endpoints in registers).
 template <typename K>
-__device__ __forceinline__ bool cand_beats(double ox, double oy, double ex, double ey, const CandT<K>& u,
-                                           const CandT<K>& v) {
+__device__ __forceinline__ bool cand_beats(const double* L, const CandT<K>& u, const CandT<K>& v) {
   if (u.idx < 0) return false;
   if (v.idx < 0) return true;
   if (u.lo > v.hi) return true;
   if (v.lo > u.hi) return false;
-  return beats_exact(ox, oy, ex, ey, u.x, u.y, u.idx, v.x, v.y, v.idx);
+  return beats_exact(L[0], L[1], L[2], L[3], u.x, u.y, u.idx, v.x, v.y, v.idx);
 }
 
 template <typename K>
@@ -353,11 +406,11 @@ __device__ __forceinline__ CandT<K> shfl_xor_cand(const CandT<K>& c, int m) {
 // Warp-wide exact argmax (all lanes get the winner).  The comparison is a
 // strict total order on distinct indices, so the butterfly is consistent.
 template <typename K>
-__device__ __forceinline__ CandT<K> warp_best(double ox, double oy, double ex, double ey, CandT<K> c) {
+__device__ __forceinline__ CandT<K> warp_best(const double* L, CandT<K> c) {
 #pragma unroll 1
   for (int m = 16; m >= 1; m >>= 1) {
     const CandT<K> o = shfl_xor_cand(c, m);
-    if (cand_beats(ox, oy, ex, ey, o, c)) c = o;
+    if (cand_beats(L, o, c)) c = o;
   }
   return c;
 }
@@ -499,10 +552,10 @@ __device__ __forceinline__ int classify_filter(const SegGeom& g, const LineF&, c
   return s2 > 0 ? 2 : 0;
 }
 
-// Exact classification (tiers 2 and 3; out-of-line calls).
-__device__ __forceinline__ int classify_exact(const SegGeom& g, double ux, double uy) {
-  if (orient_sign_slow(g.ax, g.ay, g.rx, g.ry, ux, uy) > 0) return 1;
-  if (orient_sign_slow(g.rx, g.ry, g.bx, g.by, ux, uy) > 0) return 2;
+// Exact classification (tiers 2 and 3).
+__device__ __forceinline__ int classify_exact(const SegGeom* g, double ux, double uy) {
+  if (orient_sign_slow(g->ax, g->ay, g->rx, g->ry, ux, uy) > 0) return 1;
+  if (orient_sign_slow(g->rx, g->ry, g->bx, g->by, ux, uy) > 0) return 2;
   return 0;
 }
 
@@ -515,17 +568,18 @@ __device__ __forceinline__ int classify_k(const SegGeom& g, const LineF&, const 
   return classify_slow(g, ux, uy, key, err);
 }
 
-// Key and bound of a point for one line only (farthest-point search).
-__device__ __forceinline__ void line_key_k(const LineF& L, double, double, double, double, double ux,
-                                           double uy, float& key, float& err) {
+// Key and bound of a point for one line only (farthest-point search);
+// E = {ox, oy, ex, ey} is read by the FP64 variant only.
+__device__ __forceinline__ void line_key_k(const LineF& L, const double*, double ux, double uy, float& key,
+                                           float& err) {
   const float fx = trunc_f32(ux), fy = trunc_f32(uy);
   const float m = __fadd_ru(fabsf(fx), fabsf(fy));
   orient_f32(L, fx, fy, m, key, err);
 }
-__device__ __forceinline__ void line_key_k(const LineF&, double ox, double oy, double ex, double ey,
-                                           double ux, double uy, double& key, double& err) {
+__device__ __forceinline__ void line_key_k(const LineF&, const double* E, double ux, double uy, double& key,
+                                           double& err) {
   bool sure;
-  cross_f64(ox, oy, ex, ey, ox, oy, ux, uy, key, err, sure);
+  cross_f64(E[0], E[1], E[2], E[3], E[0], E[1], ux, uy, key, err, sure);
 }
 
 }  // namespace vq

@@ -8,7 +8,7 @@
 
 namespace vq {
 
-constexpr int kK1Threads = 256;
+constexpr int kK1Threads = 128;  // partition block: 4 warps, one tile per block
 constexpr int kK0Threads = 256;
 constexpr int kK0Tile = 8192;       // points per extreme-pass tile
 constexpr int kK3Cap = 1024;        // points per warp in the small-segment kernel
@@ -38,7 +38,8 @@ struct Work {
   SegGeom* geom[2];
   int* tile_seg[2];
   unsigned long long* status[2];
-  TileCand* cand[2];
+  TileRec* cand[2];
+  SegState* sstate[2];       // per big segment: cursors and farthest-point candidates
   SegRec* k3q;
   Ctrl* ctrl;
   long long* stats;          // [3][kMaxLevels]: points read, points kept, segments
@@ -47,6 +48,7 @@ struct Work {
   int tile;                  // K1 tile size
   long long timeout_ns;
   int drop_tile;             // test knob: this K1 tile never publishes (-1: none)
+  int ordered;               // 1: offsets by decoupled look-back (stable layout); 0: atomic cursors
 };
 
 // launchers (vq_kernels.cu); all enqueue on `st`

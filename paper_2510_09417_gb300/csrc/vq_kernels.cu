@@ -80,7 +80,7 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 // Append a segment for the partition kernel (whole warp): reserve its tiles,
 // write its geometry and the tile -> segment map, clear the tiles' status.
 __device__ void push_k1_warp(const Work& w, int par, SegRec R, int lane) {
-  const int ntiles = (R.len + w.tile - 1) / w.tile;
+  const int ntiles = (R.len + w.tile - 1) / w.tile;  // w.tile = 32 * points per lane
   int slot = 0, base = 0;
   if (lane == 0) {
     slot = atomicAdd(&w.ctrl->k1_segs[par], 1);
@@ -107,6 +107,8 @@ __device__ void push_k1_warp(const Work& w, int par, SegRec R, int lane) {
     w.tile_seg[par][base + i] = slot;
     w.status[par][base + i] = 0ull;
   }
+  int* st = reinterpret_cast<int*>(&w.sstate[par][slot]);
+  for (int i = lane; i < (int)(sizeof(SegState) / sizeof(int)); i += kWarp) st[i] = 0;
 }
 
 __device__ __forceinline__ void push_k3(const Work& w, const SegRec& R) {
@@ -302,88 +304,13 @@ __global__ void k_prologue(Work w, int level) {
 // K1: fused classify + compact + per-tile argmax
 // ---------------------------------------------------------------------------
 
-template <int PPT>
-struct K1Smem {
-  SegRec seg;
-  SegGeom geom;
-  int cnt[2][PPT * (kK1Threads / kWarp)];
-  int tot[2];
-  int excl[2];
-  int tile;
-  CandT<double> wc[2][kK1Threads / kWarp];
-};
-
-// staging area of one tile (dynamic shared memory): compacted survivors,
-// left child from the front, right child from the back
-template <int PPT>
-struct K1Stage {
-  static constexpr int TILE = kK1Threads * PPT;
-  static constexpr size_t bytes = (size_t)TILE * (2 * sizeof(double) + sizeof(int));
-};
-
-// Decoupled look-back (Merrill and Garland, "Single-pass Parallel Prefix
-// Scan with Decoupled Look-back", 2016) restarted at every segment: tile t
-// publishes its (left, right) counts, then sums predecessors of the same
-// segment until one with an inclusive prefix.  Waits are bounded by
-// w.timeout_ns; on expiry the error flag is set and false returned.
-__device__ __forceinline__ bool lookback(const Work& w, int par, int t, int first, unsigned long long aggL,
-                                         unsigned long long aggR, long long& exclL, long long& exclR,
-                                         int lane) {
-  unsigned long long* st = w.status[par];
-  exclL = 0;
-  exclR = 0;
-  const bool publish = (t != w.drop_tile);
-  if (t == first) {
-    if (lane == 0 && publish) st_volatile_u64(&st[t], kStInc | st_pack(aggL, aggR));
-    return true;
-  }
-  if (lane == 0 && publish) st_volatile_u64(&st[t], kStAgg | st_pack(aggL, aggR));
-  const unsigned long long t0 = global_ns();
-  int look = t - 1;
-  bool ok = true;
-  for (;;) {
-    const int pos = look - lane;
-    unsigned long long v = 0;
-    if (pos >= first) {
-      v = ld_volatile_u64(&st[pos]);
-      while ((v & kStFlagMask) == 0) {
-        if (global_ns() - t0 > (unsigned long long)w.timeout_ns) { ok = false; break; }
-        __nanosleep(64);
-        v = ld_volatile_u64(&st[pos]);
-      }
-    }
-    ok = __all_sync(kFull, ok);
-    if (!ok) break;
-    const unsigned inc = __ballot_sync(kFull, pos >= first && (v & kStFlagMask) == kStInc);
-    const int stop = inc ? __ffs(inc) - 1 : 31;
-    long long l = 0, r = 0;
-    if (lane <= stop && pos >= first) {
-      l = (long long)((v >> 31) & kCnt31);
-      r = (long long)(v & kCnt31);
-    }
-    exclL += warp_sum_ll(l);
-    exclR += warp_sum_ll(r);
-    if (inc) break;
-    look -= kWarp;
-    if (look < first) { ok = false; break; }  // cannot happen: the first tile is inclusive
-  }
-  if (!ok) {
-    if (lane == 0) atomicOr(&w.ctrl->err, kErrTimeout);
-    return false;
-  }
-  if (lane == 0 && publish)
-    st_volatile_u64(&st[t], kStInc | st_pack((unsigned long long)exclL + aggL, (unsigned long long)exclR + aggR));
-  return true;
-}
-
 // Running exact argmax of one thread: replace the best when the new point
 // beats it (bounds first, exact tiers only when the bounds overlap).
 template <typename K>
-__device__ __forceinline__ void take_best(CandT<K>& b, double ox, double oy, double ex, double ey, double x,
-                                          double y, int idx, K key, K err) {
+__device__ __forceinline__ void take_best(CandT<K>& b, const double* L, double x, double y, int idx, K key, K err) {
   const K lo = key_lo(key, err), hi = key_hi(key, err);
   if (b.idx >= 0 && hi < b.lo) return;  // clearly nearer the line
-  if (b.idx < 0 || lo > b.hi || beats_exact(ox, oy, ex, ey, x, y, idx, b.x, b.y, b.idx)) {
+  if (b.idx < 0 || lo > b.hi || beats_exact(L[0], L[1], L[2], L[3], x, y, idx, b.x, b.y, b.idx)) {
     b.x = x; b.y = y; b.lo = lo; b.hi = hi; b.idx = idx;
   }
 }
@@ -395,52 +322,205 @@ __device__ __forceinline__ CandT<double> to_double(const CandT<K>& c) {
   return d;
 }
 
-template <int PPT, bool SRC_INPUT, bool FAST>
-__device__ __forceinline__ void k1_tile(const Work& w, int level, int t, K1Smem<PPT>& sm, double* stx, double* sty,
-                                        int* sti) {
-  typedef typename KeyOf<FAST>::T K;
-  constexpr int T = kK1Threads, W = T / kWarp, TILE = T * PPT;
-  constexpr int PER = PPT * W / kWarp;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int par = level & 1;
-  const int srcb = (level + 1) & 1, dstb = level & 1;
-  const SegRec& S = sm.seg;
-  const SegGeom& G = sm.geom;
-  const int j = t - S.tile_base;
-  const int begin = S.off + j * TILE;
-  const int count = min(TILE, S.len - j * TILE);
-  const double* __restrict__ sx = SRC_INPUT ? w.x : w.bx[srcb];
-  const double* __restrict__ sy = SRC_INPUT ? w.y : w.by[srcb];
-  const int* __restrict__ si = w.bi[srcb];
+__device__ __forceinline__ BestRec to_rec(const CandT<double>& c) {
+  BestRec r;
+  r.x = c.x; r.y = c.y; r.lo = c.lo; r.hi = c.hi; r.idx = c.idx; r.pad = 0;
+  return r;
+}
+__device__ __forceinline__ CandT<double> from_rec(const BestRec& r) {
+  CandT<double> c;
+  c.x = r.x; c.y = r.y; c.lo = r.lo; c.hi = r.hi; c.idx = r.idx;
+  return c;
+}
+__device__ __forceinline__ BestRec load_rec(const BestRec* p) {
+  BestRec r;
+  r.x = __ldcg(&p->x);
+  r.y = __ldcg(&p->y);
+  r.lo = __ldcg(&p->lo);
+  r.hi = __ldcg(&p->hi);
+  r.idx = __ldcg(&p->idx);
+  r.pad = 0;
+  return r;
+}
 
-  // A: load, classify, running exact argmax per child (each warp reads 32
-  // consecutive points per round)
-  double px[PPT], py[PPT];
-  int pi[PPT];
+// Decoupled look-back (Merrill and Garland, "Single-pass Parallel Prefix
+// Scan with Decoupled Look-back", 2016), restarted at every segment, carrying
+// two sums (left and right child counts) and two running maxima (the
+// children's farthest points under the exact order).  Tile t publishes its
+// own counts and farthest points (aggregate), then combines predecessors of
+// the same segment until one with an inclusive prefix, then publishes its
+// inclusive prefix.  Records are written before the status word that makes
+// them visible (release); readers load the status with acquire.  Waits are
+// bounded by w.timeout_ns; on expiry the error flag is set and false returned.
+__device__ __forceinline__ bool lookback_warp(const Work& w, int par, int t, int first, const SegGeom* G,
+                                              unsigned long long aggL, unsigned long long aggR,
+                                              const CandT<double>& own0, const CandT<double>& own1,
+                                              long long& exclL, long long& exclR, CandT<double>& incl0,
+                                              CandT<double>& incl1, int lane) {
+  unsigned long long* st = w.status[par];
+  TileRec* rec = w.cand[par];
+  exclL = 0;
+  exclR = 0;
+  const bool publish = (t != w.drop_tile);
+  incl0 = own0;
+  incl1 = own1;
+  if (t == first) {
+    if (lane == 0) {
+      rec[t].incl[0] = to_rec(own0);
+      rec[t].incl[1] = to_rec(own1);
+      if (publish) st_release_u64(&st[t], kStInc | st_pack(aggL, aggR));
+    }
+    return true;
+  }
+  if (lane == 0) {
+    rec[t].own[0] = to_rec(own0);
+    rec[t].own[1] = to_rec(own1);
+    if (publish) st_release_u64(&st[t], kStAgg | st_pack(aggL, aggR));
+  }
+  const unsigned long long t0 = global_ns();
+  CandT<double> acc0 = own0, acc1 = own1;
+  int look = t - 1;
+  bool ok = true;
+  for (;;) {
+    const int pos = look - lane;
+    unsigned long long v = 0;
+    if (pos >= first) {
+      v = ld_acquire_u64(&st[pos]);
+      while ((v & kStFlagMask) == 0) {
+        if (global_ns() - t0 > (unsigned long long)w.timeout_ns) { ok = false; break; }
+        __nanosleep(32);
+        v = ld_acquire_u64(&st[pos]);
+      }
+    }
+    ok = __all_sync(kFull, ok);
+    if (!ok) break;
+    const unsigned inc = __ballot_sync(kFull, pos >= first && (v & kStFlagMask) == kStInc);
+    const int stop = inc ? __ffs(inc) - 1 : 31;
+    long long l = 0, r = 0;
+    CandT<double> c0 = cand_none<double>(), c1 = cand_none<double>();
+    if (lane <= stop && pos >= first) {
+      l = (long long)((v >> 31) & kCnt31);
+      r = (long long)(v & kCnt31);
+      const bool isinc = (v & kStFlagMask) == kStInc;
+      c0 = from_rec(load_rec(isinc ? &rec[pos].incl[0] : &rec[pos].own[0]));
+      c1 = from_rec(load_rec(isinc ? &rec[pos].incl[1] : &rec[pos].own[1]));
+    }
+    exclL += warp_sum_ll(l);
+    exclR += warp_sum_ll(r);
+    if (__any_sync(kFull, c0.idx >= 0)) {
+      c0 = warp_best(&G->ax, c0);
+      if (cand_beats(&G->ax, c0, acc0)) acc0 = c0;
+    }
+    if (__any_sync(kFull, c1.idx >= 0)) {
+      c1 = warp_best(&G->rx, c1);
+      if (cand_beats(&G->rx, c1, acc1)) acc1 = c1;
+    }
+    if (inc) break;
+    look -= kWarp;
+    if (look < first) { ok = false; break; }  // cannot happen: the first tile is inclusive
+  }
+  if (!ok) {
+    if (lane == 0) atomicOr(&w.ctrl->err, kErrTimeout);
+    return false;
+  }
+  if (lane == 0) {
+    rec[t].incl[0] = to_rec(acc0);
+    rec[t].incl[1] = to_rec(acc1);
+    if (publish)
+      st_release_u64(&st[t], kStInc | st_pack((unsigned long long)exclL + aggL, (unsigned long long)exclR + aggR));
+  }
+  incl0 = acc0;
+  incl1 = acc1;
+  return true;
+}
+
+// Unordered offsets and farthest-point candidates for one tile (lane 0 of
+// warp 0): one 64-bit atomic on the segment's cursor returns both children's
+// output offsets; the tile's best per child is published as a candidate when
+// its upper bound reaches the largest lower bound seen so far.  The true
+// farthest point's tile always qualifies (its upper bound is at least every
+// tile's lower bound), so it is always listed.
+__device__ __forceinline__ void tile_atomic(const Work& w, int par, int sid, int t, unsigned long long cnt0,
+                                            unsigned long long cnt1, const CandT<double>& c0,
+                                            const CandT<double>& c1, long long& eL, long long& eR) {
+  SegState* st = &w.sstate[par][sid];
+  const unsigned long long old = atomicAdd(&st->cursor, (cnt0 << 32) | cnt1);
+  eL = (long long)(old >> 32);
+  eR = (long long)(old & 0xffffffffull);
+  TileRec* rec = &w.cand[par][t];
+  rec->own[0] = to_rec(c0);
+  rec->own[1] = to_rec(c1);
 #pragma unroll
-  for (int k = 0; k < PPT; k++) {
-    const int l = k * T + tid;
-    px[k] = 0.0; py[k] = 0.0; pi[k] = 0;
-    if (l < count && VQ_OK_IDX(w, 7, (long long)begin + l, 0, w.N)) {
-      px[k] = __ldcs(sx + begin + l);
-      py[k] = __ldcs(sy + begin + l);
-      pi[k] = SRC_INPUT ? begin + l : __ldcs(si + begin + l);
-#ifdef VQ_CHECKED
-      if (!VQ_OK_IDX(w, 8, pi[k], 0, w.N)) pi[k] = 0;
-#endif
+  for (int ch = 0; ch < 2; ch++) {
+    const CandT<double>& c = ch ? c1 : c0;
+    if (c.idx < 0) continue;
+    const unsigned long long klo = dkey(c.lo);
+    const unsigned long long prev = atomicMax(&st->lomax[ch], klo);
+    const unsigned long long thr = prev > klo ? prev : klo;
+    if (dkey(c.hi) >= thr) {
+      const int i = atomicAdd(&st->ncand[ch], 1);
+      if (i < kMaxCand) st->cand[ch][i] = t;
     }
   }
-  // pass 1: filter only, no calls; undecided points are flagged.  Per child
-  // the largest lower bound of the key (farthest-point search) is kept.
+}
+
+// ---- asynchronous global -> shared copies (cp.async, per thread) ----
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory layout of the partition kernel: an input stage (the tile's
+// points, copied asynchronously) and an output stage (the compacted
+// survivors), each split into one region per warp.
+template <int PPT>
+struct K1Layout {
+  static constexpr int WPB = kK1Threads / kWarp;
+  static constexpr int TW = kWarp * PPT;     // points per warp
+  static constexpr int TB = WPB * TW;        // points per block tile
+  static constexpr size_t bytes = 2ull * TB * (2 * sizeof(double) + sizeof(int));
+};
+
+struct K1Shared {
+  int tot[2][kK1Threads / kWarp];
+  int pre[2][kK1Threads / kWarp];
+  CandT<double> best[2][kK1Threads / kWarp];
+  int excl[2];
+  int tick;
+};
+
+// Warp part of a block tile: classify this warp's points (read from its
+// input region), find its exact farthest point per child, compact the
+// survivors into its output region (left child from the start, right child
+// from the end).  Points are re-read from shared memory in each pass, so no
+// per-point registers are held across the rare exact paths.
+template <int PPT, bool SRC_INPUT, bool FAST>
+__device__ __forceinline__ void k1_warp_part(const Work& w, const SegRec& S, const SegGeom* __restrict__ G, int j,
+                                             const double* ix, const double* iy, const int* ii, double* ox_,
+                                             double* oy_, int* oi_, int warp, int lane, int& tot0, int& tot1,
+                                             CandT<double>& best0, CandT<double>& best1) {
+  typedef typename KeyOf<FAST>::T K;
+  typedef K1Layout<PPT> Ly;
+  const int begin = S.off + j * Ly::TB + warp * Ly::TW;
+  const int count = S.len - j * Ly::TB - warp * Ly::TW;
+  // pass 1: filter only; undecided points are flagged
   unsigned cls = 0, und = 0;
   K lo0 = key_neg_inf<K>(), lo1 = key_neg_inf<K>();
-  const LineF l1 = line1_of(G), l2 = line2_of(G);
+  const LineF l1 = line1_of(*G), l2 = line2_of(*G);
 #pragma unroll
   for (int k = 0; k < PPT; k++) {
-    const int l = k * T + tid;
+    const int l = k * kWarp + lane;
     if (l < count) {
       K key, err;
-      const int c = classify_filter(G, l1, l2, px[k], py[k], key, err);
+      const int c = classify_filter(*G, l1, l2, ix[l], iy[l], key, err);
       if (c == 3) {
         und |= 1u << k;
       } else {
@@ -451,163 +531,205 @@ __device__ __forceinline__ void k1_tile(const Work& w, int level, int t, K1Smem<
     }
   }
   // pass 2 (rare): exact classification of the undecided points
-  if (und) {
-#pragma unroll
+  if (__any_sync(kFull, und != 0)) {
+#pragma unroll 1
     for (int k = 0; k < PPT; k++) {
       if (!((und >> k) & 1u)) continue;
-      const int c = classify_exact(G, px[k], py[k]);
+      const int l = k * kWarp + lane;
+      const double ux = ix[l], uy = iy[l];
+      const int c = classify_exact(G, ux, uy);
       cls |= (unsigned)c << (2 * k);
       if (c != 0) {
         K key, err;
-        if (c == 1) line_key_k(l1, G.ax, G.ay, G.rx, G.ry, px[k], py[k], key, err);
-        else line_key_k(l2, G.rx, G.ry, G.bx, G.by, px[k], py[k], key, err);
+        if (c == 1) line_key_k(l1, &G->ax, ux, uy, key, err);
+        else line_key_k(l2, &G->rx, ux, uy, key, err);
         if (c == 1) lo0 = key_max(lo0, key_lo(key, err));
         else lo1 = key_max(lo1, key_lo(key, err));
       }
     }
   }
-  // pass 3: this thread's exact farthest point per child among the points
-  // whose upper bound reaches the thread's best lower bound
+  // pass 3: exact farthest point per child; candidates are the points whose
+  // upper bound reaches the warp's best lower bound
+  const K L0 = warp_max_k(lo0), L1 = warp_max_k(lo1);
   CandT<K> b0 = cand_none<K>(), b1 = cand_none<K>();
 #pragma unroll
   for (int k = 0; k < PPT; k++) {
     const unsigned c = (cls >> (2 * k)) & 3u;
     if (c == 0u) continue;
+    const int l = k * kWarp + lane;
+    const double ux = ix[l], uy = iy[l];
     K key, err;
-    if (c == 1u) line_key_k(l1, G.ax, G.ay, G.rx, G.ry, px[k], py[k], key, err);
-    else line_key_k(l2, G.rx, G.ry, G.bx, G.by, px[k], py[k], key, err);
-    if (key_hi(key, err) < (c == 1u ? lo0 : lo1)) continue;
-    if (c == 1u) take_best(b0, G.ax, G.ay, G.rx, G.ry, px[k], py[k], pi[k], key, err);
-    else take_best(b1, G.rx, G.ry, G.bx, G.by, px[k], py[k], pi[k], key, err);
+    if (c == 1u) line_key_k(l1, &G->ax, ux, uy, key, err);
+    else line_key_k(l2, &G->rx, ux, uy, key, err);
+    if (key_hi(key, err) < (c == 1u ? L0 : L1)) continue;
+    const int id = SRC_INPUT ? begin + l : ii[l];
+    if (c == 1u) take_best(b0, &G->ax, ux, uy, id, key, err);
+    else take_best(b1, &G->rx, ux, uy, id, key, err);
   }
+  if (__any_sync(kFull, b0.idx >= 0)) b0 = warp_best(&G->ax, b0);
+  if (__any_sync(kFull, b1.idx >= 0)) b1 = warp_best(&G->rx, b1);
+  best0 = to_double(b0);
+  best1 = to_double(b1);
+  // compaction into the output region, in point order per child
+  tot0 = 0;
+  tot1 = 0;
+  const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int k = 0; k < PPT; k++) {
     const unsigned c = (cls >> (2 * k)) & 3u;
     const unsigned mL = __ballot_sync(kFull, c == 1u), mR = __ballot_sync(kFull, c == 2u);
-    if (lane == 0) {
-      sm.cnt[0][k * W + warp] = __popc(mL);
-      sm.cnt[1][k * W + warp] = __popc(mR);
+    int q = -1;
+    if (c == 1u) q = tot0 + __popc(mL & lt);
+    else if (c == 2u) q = Ly::TW - 1 - (tot1 + __popc(mR & lt));
+    if (q >= 0) {
+      const int l = k * kWarp + lane;
+      ox_[q] = ix[l];
+      oy_[q] = iy[l];
+      oi_[q] = SRC_INPUT ? begin + l : ii[l];
     }
+    tot0 += __popc(mL);
+    tot1 += __popc(mR);
   }
-  __syncthreads();
-
-  // B: warp 0 scans the (round, warp) counts in round-major order, so a
-  // survivor's rank is its position among its child's survivors in the
-  // original point order
-  if (warp == 0) {
-#pragma unroll
-    for (int ch = 0; ch < 2; ch++) {
-      int v[PER];
-      int sum = 0;
-#pragma unroll
-      for (int q = 0; q < PER; q++) { v[q] = sm.cnt[ch][lane * PER + q]; sum += v[q]; }
-      int incl = sum;
-#pragma unroll
-      for (int o = 1; o < kWarp; o <<= 1) {
-        const int n = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += n;
-      }
-      int run = incl - sum;
-#pragma unroll
-      for (int q = 0; q < PER; q++) { sm.cnt[ch][lane * PER + q] = run; run += v[q]; }
-      if (lane == 31) sm.tot[ch] = incl;
-    }
-  }
-  __syncthreads();
-
-  // C: scatter survivors into the stage; reduce the argmax over the warp
-  {
-    const unsigned lt = lanemask_lt();
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-      const unsigned c = (cls >> (2 * k)) & 3u;
-      const unsigned mL = __ballot_sync(kFull, c == 1u), mR = __ballot_sync(kFull, c == 2u);
-      int pos = -1;
-      if (c == 1u) pos = sm.cnt[0][k * W + warp] + __popc(mL & lt);
-      else if (c == 2u) pos = TILE - 1 - (sm.cnt[1][k * W + warp] + __popc(mR & lt));
-      if (pos >= 0) { stx[pos] = px[k]; sty[pos] = py[k]; sti[pos] = pi[k]; }
-    }
-  }
-  if (__any_sync(kFull, b0.idx >= 0)) b0 = warp_best(G.ax, G.ay, G.rx, G.ry, b0);
-  if (__any_sync(kFull, b1.idx >= 0)) b1 = warp_best(G.rx, G.ry, G.bx, G.by, b1);
-  if (lane == 0) { sm.wc[0][warp] = to_double(b0); sm.wc[1][warp] = to_double(b1); }
-  __syncthreads();
-
-  // D: warp 0 finds the tile's offsets (look-back); warp 1 reduces the
-  // per-warp winners into the tile's candidates
-  const int tot0 = sm.tot[0], tot1 = sm.tot[1];
-  if (warp == 0) {
-    long long eL, eR;
-    const bool ok = lookback(w, par, t, S.tile_base, (unsigned long long)tot0, (unsigned long long)tot1, eL, eR, lane);
-    if (lane == 0) {
-      sm.excl[0] = ok ? (int)eL : -1;
-      sm.excl[1] = ok ? (int)eR : -1;
-    }
-  } else if (warp == 1) {
-    CandT<double> c0 = cand_none<double>(), c1 = cand_none<double>();
-    if (lane < W) { c0 = sm.wc[0][lane]; c1 = sm.wc[1][lane]; }
-    c0 = warp_best(G.ax, G.ay, G.rx, G.ry, c0);
-    c1 = warp_best(G.rx, G.ry, G.bx, G.by, c1);
-    if (lane == 0) {
-      TileCand tc;
-      tc.idx[0] = c0.idx; tc.lo[0] = c0.lo; tc.hi[0] = c0.hi;
-      tc.idx[1] = c1.idx; tc.lo[1] = c1.lo; tc.hi[1] = c1.hi;
-      w.cand[par][t] = tc;
-    }
-  }
-  __syncthreads();
-
-  // E: contiguous copy-out: left child forward from S.off + eL, right child
-  // (stored reversed at the stage's end) backward from the segment end
-  const int eL = sm.excl[0], eR = sm.excl[1];
-  if (eL >= 0 && eL + tot0 <= S.len && eR + tot1 <= S.len &&
-      VQ_OK_IDX(w, 9, (long long)S.off + S.len, 1, (long long)w.N + 1) && VQ_OK_IDX(w, 10, S.off, 0, w.N)) {
-    double* __restrict__ dx = w.bx[dstb];
-    double* __restrict__ dy = w.by[dstb];
-    int* __restrict__ di = w.bi[dstb];
-    const int l0 = S.off + eL;
-    for (int i = tid; i < tot0; i += T) {
-      __stcs(dx + l0 + i, stx[i]);
-      __stcs(dy + l0 + i, sty[i]);
-      __stcs(di + l0 + i, sti[i]);
-    }
-    const int r0 = S.off + S.len - eR - tot1;  // global position of stage index TILE - tot1
-    for (int i = tid; i < tot1; i += T) {
-      const int q = TILE - tot1 + i;
-      __stcs(dx + r0 + i, stx[q]);
-      __stcs(dy + r0 + i, sty[q]);
-      __stcs(di + r0 + i, sti[q]);
-    }
-  }
+  __syncwarp();
 }
 
+// Partition kernel: one block per tile.  A block takes the next tile number
+// when it starts (so tiles are processed in claim order and a look-back only
+// waits for tiles already in progress), copies the tile's points into shared
+// memory (cp.async), lets its warps classify and compact their parts
+// independently, combines their counts and farthest points, runs the
+// segment's decoupled look-back (warp 0) and writes the survivors out with
+// contiguous, coalesced stores.
 template <int PPT, bool SRC_INPUT>
-__global__ void __launch_bounds__(kK1Threads, 2) k_k1(Work w, int level) {
-  __shared__ K1Smem<PPT> sm;
-  extern __shared__ __align__(16) unsigned char k1_dyn[];
-  constexpr int TILE = kK1Threads * PPT;
-  double* stx = reinterpret_cast<double*>(k1_dyn);
-  double* sty = stx + TILE;
-  int* sti = reinterpret_cast<int*>(sty + TILE);
+__global__ void __launch_bounds__(kK1Threads) k_k1(Work w, int level) {
+  typedef K1Layout<PPT> Ly;
+  constexpr int WPB = Ly::WPB, TW = Ly::TW, TB = Ly::TB;
+  extern __shared__ __align__(16) unsigned char k1_smem[];
+  __shared__ K1Shared sh;
   if (fatal(w)) return;
   const int par = level & 1;
+  const int srcb = (level + 1) & 1, dstb = level & 1;
   const int ntiles = min(*reinterpret_cast<volatile int*>(&w.ctrl->k1_tiles[par]), w.capT);
-  const int tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) sm.tile = atomicAdd(&w.ctrl->k1_ticket, 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int t = blockIdx.x;
+  if (w.ordered) {  // the look-back needs tiles in start order
+    if (tid == 0) sh.tick = atomicAdd(&w.ctrl->k1_ticket, 1);
     __syncthreads();
-    const int t = sm.tile;
-    if (t >= ntiles) break;
-    const int sid = w.tile_seg[par][t];
-    if (!VQ_OK_IDX(w, 20, sid, 0, w.capS)) break;
-    constexpr int SW = sizeof(SegRec) / 4, GW = sizeof(SegGeom) / 4;
-    if (tid < SW) reinterpret_cast<int*>(&sm.seg)[tid] = reinterpret_cast<const int*>(&w.segs[par][sid])[tid];
-    else if (tid < SW + GW)
-      reinterpret_cast<int*>(&sm.geom)[tid - SW] = reinterpret_cast<const int*>(&w.geom[par][sid])[tid - SW];
-    __syncthreads();
-    if (sm.seg.flags & kSegFast) k1_tile<PPT, SRC_INPUT, true>(w, level, t, sm, stx, sty, sti);
-    else k1_tile<PPT, SRC_INPUT, false>(w, level, t, sm, stx, sty, sti);
-    __syncthreads();
+    t = sh.tick;
+  }
+  if (t >= ntiles) return;
+  const int sid = __ldg(&w.tile_seg[par][t]);
+#ifdef VQ_CHECKED
+  if (!VQ_OK_IDX(w, 20, sid, 0, w.capS)) return;
+#endif
+  const SegRec S = w.segs[par][sid];
+  const SegGeom* G = &w.geom[par][sid];
+  const int j = t - S.tile_base;
+  double* const base = reinterpret_cast<double*>(k1_smem);
+  double* ix = base + warp * TW;
+  double* iy = base + TB + warp * TW;
+  double* ox_ = base + 2 * TB + warp * TW;
+  double* oy_ = base + 3 * TB + warp * TW;
+  int* ii = reinterpret_cast<int*>(base + 4 * TB) + warp * TW;
+  int* oi_ = reinterpret_cast<int*>(base + 4 * TB) + TB + warp * TW;
+  {
+    const int begin = S.off + j * TB + warp * TW;
+    const int count = S.len - j * TB - warp * TW;
+    const double* sx = SRC_INPUT ? w.x : w.bx[srcb];
+    const double* sy = SRC_INPUT ? w.y : w.by[srcb];
+    const int* si = w.bi[srcb];
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      const int l = k * kWarp + lane;
+      if (l < count && VQ_OK_IDX(w, 7, (long long)begin + l, 0, w.N)) {
+        cp_async8(ix + l, sx + begin + l);
+        cp_async8(iy + l, sy + begin + l);
+        if (!SRC_INPUT) cp_async4(ii + l, si + begin + l);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();  // each lane reads back only what it copied
+  }
+  int tot0, tot1;
+  CandT<double> best0, best1;
+  if (S.flags & kSegFast)
+    k1_warp_part<PPT, SRC_INPUT, true>(w, S, G, j, ix, iy, ii, ox_, oy_, oi_, warp, lane, tot0, tot1, best0, best1);
+  else
+    k1_warp_part<PPT, SRC_INPUT, false>(w, S, G, j, ix, iy, ii, ox_, oy_, oi_, warp, lane, tot0, tot1, best0, best1);
+  if (lane == 0) {
+    sh.tot[0][warp] = tot0;
+    sh.tot[1][warp] = tot1;
+    sh.best[0][warp] = best0;
+    sh.best[1][warp] = best1;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // warp prefixes, block totals, block farthest points, then the
+    // segment's look-back for this tile
+    const int t0 = lane < WPB ? sh.tot[0][lane] : 0, t1 = lane < WPB ? sh.tot[1][lane] : 0;
+    int i0 = t0, i1 = t1;
+#pragma unroll
+    for (int o = 1; o < WPB; o <<= 1) {
+      const int n0 = __shfl_up_sync(kFull, i0, o), n1 = __shfl_up_sync(kFull, i1, o);
+      if (lane >= o) { i0 += n0; i1 += n1; }
+    }
+    if (lane < WPB) { sh.pre[0][lane] = i0 - t0; sh.pre[1][lane] = i1 - t1; }
+    const int bt0 = __shfl_sync(kFull, i0, WPB - 1), bt1 = __shfl_sync(kFull, i1, WPB - 1);
+    CandT<double> c0 = cand_none<double>(), c1 = cand_none<double>();
+    if (lane < WPB) { c0 = sh.best[0][lane]; c1 = sh.best[1][lane]; }
+    if (__any_sync(kFull, c0.idx >= 0)) c0 = warp_best(&G->ax, c0);
+    if (__any_sync(kFull, c1.idx >= 0)) c1 = warp_best(&G->rx, c1);
+    long long eL = 0, eR = 0;
+    bool ok = true;
+    if (w.ordered) {
+      CandT<double> i0c, i1c;
+      ok = lookback_warp(w, par, t, S.tile_base, G, (unsigned long long)bt0, (unsigned long long)bt1, c0, c1, eL, eR,
+                         i0c, i1c, lane);
+      if (ok && lane == 0 && t == S.tile_base + S.ntiles - 1) {
+        // last tile: publish the segment's totals and farthest points in the
+        // form the finalize kernel reads
+        SegState* st = &w.sstate[par][sid];
+        st->cursor = ((unsigned long long)(eL + bt0) << 32) | (unsigned long long)(eR + bt1);
+        w.cand[par][t].own[0] = to_rec(i0c);
+        w.cand[par][t].own[1] = to_rec(i1c);
+        for (int ch = 0; ch < 2; ch++) {
+          const CandT<double>& c = ch ? i1c : i0c;
+          st->lomax[ch] = c.idx >= 0 ? dkey(c.lo) : 0ull;
+          st->ncand[ch] = c.idx >= 0 ? 1 : 0;
+          st->cand[ch][0] = t;
+        }
+      }
+    } else if (lane == 0) {
+      tile_atomic(w, par, sid, t, (unsigned long long)bt0, (unsigned long long)bt1, c0, c1, eL, eR);
+    }
+    if (lane == 0) {
+      const bool fits = ok && eL + bt0 <= S.len && eR + bt1 <= S.len;
+      sh.excl[0] = fits ? (int)eL : -1;
+      sh.excl[1] = fits ? (int)eR : -1;
+    }
+  }
+  __syncthreads();
+  const int eL = sh.excl[0], eR = sh.excl[1];
+  if (eL < 0) return;
+#ifdef VQ_CHECKED
+  if (!VQ_OK_IDX(w, 9, (long long)S.off + S.len, 1, (long long)w.N + 1) || !VQ_OK_IDX(w, 10, S.off, 0, w.N)) return;
+#endif
+  // contiguous copy-out of this warp's survivors
+  double* __restrict__ dx = w.bx[dstb];
+  double* __restrict__ dy = w.by[dstb];
+  int* __restrict__ di = w.bi[dstb];
+  const int l0 = S.off + eL + sh.pre[0][warp];
+  for (int i = lane; i < tot0; i += kWarp) {
+    __stcs(dx + l0 + i, ox_[i]);
+    __stcs(dy + l0 + i, oy_[i]);
+    __stcs(di + l0 + i, oi_[i]);
+  }
+  const int r0 = S.off + S.len - eR - sh.pre[1][warp] - tot1;
+  for (int i = lane; i < tot1; i += kWarp) {
+    const int q = TW - tot1 + i;
+    __stcs(dx + r0 + i, ox_[q]);
+    __stcs(dy + r0 + i, oy_[q]);
+    __stcs(di + r0 + i, oi_[q]);
   }
 }
 
@@ -615,24 +737,31 @@ __global__ void __launch_bounds__(kK1Threads, 2) k_k1(Work w, int level) {
 // K2: per segment, cross-tile argmax, emission, children
 // ---------------------------------------------------------------------------
 
-__device__ CandT<double> reduce_tiles(const Work& w, int par, const SegRec& S, int ch, double ox, double oy,
-                                      double ex, double ey, int lane) {
-  const int end = S.tile_base + S.ntiles;
+// Child ch's farthest point from the segment's candidate list (exact), or
+// from every tile's record when the list overflowed.
+__device__ BestRec seg_best(const Work& w, int par, int s, const SegRec& S, int ch, const double* L, int lane) {
+  const SegState* st = &w.sstate[par][s];
+  const int nc = __ldcg(&st->ncand[ch]);
+  const double thr = dkey_inv(__ldcg(&st->lomax[ch]));
   CandT<double> best = cand_none<double>();
-  for (int t = S.tile_base + lane; t < end; t += kWarp) {
-    const TileCand& c = w.cand[par][t];
-    const int idx = c.idx[ch];
-    if (idx < 0 || (best.idx >= 0 && c.hi[ch] < best.lo)) continue;
-    if (!VQ_OK_IDX(w, 11, idx, 0, w.N)) continue;
-    CandT<double> cc;
-    cc.idx = idx;
-    cc.lo = c.lo[ch];
-    cc.hi = c.hi[ch];
-    cc.x = w.x[idx];
-    cc.y = w.y[idx];
-    if (cand_beats(ox, oy, ex, ey, cc, best)) best = cc;
+  if (nc <= kMaxCand) {
+    for (int i = lane; i < nc; i += kWarp) {
+      const int t = __ldcg(&st->cand[ch][i]);
+      const BestRec r = load_rec(&w.cand[par][t].own[ch]);
+      if (r.idx < 0 || r.hi < thr) continue;
+      const CandT<double> c = from_rec(r);
+      if (cand_beats(L, c, best)) best = c;
+    }
+  } else {
+    for (int t = S.tile_base + lane; t < S.tile_base + S.ntiles; t += kWarp) {
+      const BestRec r = load_rec(&w.cand[par][t].own[ch]);
+      if (r.idx < 0 || r.hi < thr) continue;
+      const CandT<double> c = from_rec(r);
+      if (cand_beats(L, c, best)) best = c;
+    }
   }
-  return warp_best(ox, oy, ex, ey, best);
+  best = warp_best(L, best);
+  return to_rec(best);
 }
 
 __device__ void make_child(const Work& w, const SegRec& P, int a, int b, int r, int off, int len, int level,
@@ -675,14 +804,21 @@ __global__ void k_k2(Work w, int level) {
     const SegRec S = w.segs[par][s];
     const SegGeom& G = w.geom[par][s];
     const double ax = G.ax, ay = G.ay, rx = G.rx, ry = G.ry, bx = G.bx, by = G.by;
-    const unsigned long long last = ld_volatile_u64(&w.status[par][S.tile_base + S.ntiles - 1]);
-    if ((last & kStFlagMask) != kStInc) {
-      if (lane == 0) atomicOr(&w.ctrl->err, kErrTimeout);
+    (void)ax; (void)ay; (void)rx; (void)ry; (void)bx; (void)by;
+    const unsigned long long cur = __ldcg(&w.sstate[par][s].cursor);
+    const int nL = (int)(cur >> 32), nR = (int)(cur & 0xffffffffull);
+    if (nL + nR > S.len) {
+      if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
       continue;
     }
-    const int nL = (int)((last >> 31) & kCnt31), nR = (int)(last & kCnt31);
-    const CandT<double> bl = reduce_tiles(w, par, S, 0, ax, ay, rx, ry, lane);
-    const CandT<double> br = reduce_tiles(w, par, S, 1, rx, ry, bx, by, lane);
+    BestRec bl, br;
+    bl.idx = -1;
+    br.idx = -1;
+    if (nL > 0) bl = seg_best(w, par, s, S, 0, &w.geom[par][s].ax, lane);
+    if (nR > 0) br = seg_best(w, par, s, S, 1, &w.geom[par][s].rx, lane);
+#ifdef VQ_CHECKED
+    if ((nL > 0 && !VQ_OK_IDX(w, 11, bl.idx, 0, w.N)) || (nR > 0 && !VQ_OK_IDX(w, 11, br.idx, 0, w.N))) continue;
+#endif
     if (lane == 0) {
       emit(w, (long long)S.off + nL + 1 + S.shift, S.r - S.set_off);
       add_stats(w, S.level, S.len, nL + nR);
@@ -705,25 +841,29 @@ struct Frame {
   int depth;
 };
 
+// Exact farthest point of P[lo, hi) from the line E = {ox, oy, ex, ey}
+// (E in shared memory, read only by the exact tiers and the FP64 keys).
 template <bool FAST>
 __device__ int small_argmax(const double* X, const double* Y, const int* I, const unsigned short* P, int lo,
-                            int hi, double ox, double oy, double ex, double ey, int lane) {
+                            int hi, const double* E, int lane) {
   typedef typename KeyOf<FAST>::T K;
   LineF L;
-  if (FAST) L = make_line(ox, oy, ex, ey);
+  if (FAST) L = make_line(E[0], E[1], E[2], E[3]);
   CandT<K> best = cand_none<K>();
   for (int l = lo + lane; l < hi; l += kWarp) {
     const int u = P[l];
     K key, err;
-    line_key_k(L, ox, oy, ex, ey, X[u], Y[u], key, err);
-    take_best(best, ox, oy, ex, ey, X[u], Y[u], I[u], key, err);
+    line_key_k(L, E, X[u], Y[u], key, err);
+    take_best(best, E, X[u], Y[u], I[u], key, err);
   }
-  best = warp_best(ox, oy, ex, ey, best);
+  best = warp_best(E, best);
   return best.idx;
 }
 
+// One warp finishes a segment of <= kK3Cap points held in shared memory:
+// Alg. 1's recursion with an explicit stack, one partition per step.
 __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y, int* I, unsigned short* P0,
-                            unsigned short* P1, Frame* stk, int lane) {
+                            unsigned short* P1, Frame* stk, SegGeom* G, double* E, int lane) {
   const bool fast = (S.flags & kSegFast) != 0;
   const unsigned lt = lanemask_lt();
   int top = 0;
@@ -743,21 +883,21 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
       return;
     unsigned short* Pin = f.buf ? P1 : P0;
     unsigned short* Pout = f.buf ? P0 : P1;
-    const double ax = w.x[f.a], ay = w.y[f.a], bx = w.x[f.b], by = w.y[f.b];
+    if (lane == 0) { E[0] = w.x[f.a]; E[1] = w.y[f.a]; E[2] = w.x[f.b]; E[3] = w.y[f.b]; }
+    __syncwarp();
     int r = f.r;
     if (r < 0)
-      r = fast ? small_argmax<true>(X, Y, I, Pin, f.lo, f.hi, ax, ay, bx, by, lane)
-               : small_argmax<false>(X, Y, I, Pin, f.lo, f.hi, ax, ay, bx, by, lane);
+      r = fast ? small_argmax<true>(X, Y, I, Pin, f.lo, f.hi, E, lane)
+               : small_argmax<false>(X, Y, I, Pin, f.lo, f.hi, E, lane);
     if (r < 0) {
       if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
       return;
     }
     if (!VQ_OK_IDX(w, 16, r, 0, w.N)) return;
-    const double rx = w.x[r], ry = w.y[r];
-    SegGeom G;
-    G.ax = ax; G.ay = ay; G.bx = bx; G.by = by; G.rx = rx; G.ry = ry;
+    if (lane == 0) fill_geom(*G, E[0], E[1], E[2], E[3], w.x[r], w.y[r]);
+    __syncwarp();
     LineF l1, l2;
-    if (fast) { l1 = make_line(ax, ay, rx, ry); l2 = make_line(rx, ry, bx, by); }
+    if (fast) { l1 = line1_of(*G); l2 = line2_of(*G); }
     int nL = 0, nR = 0;
     for (int base = f.lo; base < f.hi; base += kWarp) {
       const int l = base + lane;
@@ -765,8 +905,9 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
       unsigned short u = 0;
       if (l < f.hi) {
         u = Pin[l];
-        if (fast) { float k, e; c = classify_fast(G, l1, l2, X[u], Y[u], k, e); }
-        else { double k, e; c = classify_slow(G, X[u], Y[u], k, e); }
+        if (fast) { float k, e; c = classify_filter(*G, l1, l2, X[u], Y[u], k, e); }
+        else { double k, e; c = classify_filter(*G, l1, l2, X[u], Y[u], k, e); }
+        if (c == 3) c = classify_exact(G, X[u], Y[u]);
       }
       const unsigned mL = __ballot_sync(kFull, c == 1), mR = __ballot_sync(kFull, c == 2);
       if (c == 1) Pout[f.lo + nL + __popc(mL & lt)] = u;
@@ -809,18 +950,22 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
   }
 }
 
+static constexpr size_t kK3PerWarp =
+    (size_t)kK3Cap * 24 + sizeof(Frame) * kK3Stack + sizeof(SegGeom) + 4 * sizeof(double);
+
 __global__ void __launch_bounds__(kK3Warps * kWarp) k_k3(Work w) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (fatal(w)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const size_t per = (size_t)kK3Cap * 24 + sizeof(Frame) * kK3Stack;
-  unsigned char* base = smem + per * warp;
+  unsigned char* base = smem + kK3PerWarp * warp;
   double* X = reinterpret_cast<double*>(base);
   double* Y = X + kK3Cap;
   int* I = reinterpret_cast<int*>(Y + kK3Cap);
   unsigned short* P0 = reinterpret_cast<unsigned short*>(I + kK3Cap);
   unsigned short* P1 = P0 + kK3Cap;
-  Frame* stk = reinterpret_cast<Frame*>(P1 + kK3Cap);
+  SegGeom* G = reinterpret_cast<SegGeom*>(P1 + kK3Cap);  // 8-byte aligned: 24 * kK3Cap bytes precede it
+  double* E = reinterpret_cast<double*>(G + 1);
+  Frame* stk = reinterpret_cast<Frame*>(E + 4);
   const int nq = min(*reinterpret_cast<volatile int*>(&w.ctrl->k3_count), w.capQ);
   for (int e = blockIdx.x * kK3Warps + warp; e < nq; e += gridDim.x * kK3Warps) {
     const SegRec S = w.k3q[e];
@@ -846,7 +991,7 @@ __global__ void __launch_bounds__(kK3Warps * kWarp) k_k3(Work w) {
       P0[l] = (unsigned short)l;
     }
     __syncwarp();
-    small_solve(w, S, X, Y, I, P0, P1, stk, lane);
+    small_solve(w, S, X, Y, I, P0, P1, stk, G, E, lane);
     __syncwarp();
   }
 }
@@ -1061,16 +1206,20 @@ cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st) {
 }
 
 template <int PPT>
+static size_t k1_smem() {
+  return K1Layout<PPT>::bytes;
+}
+
+template <int PPT>
 static cudaError_t k1_attrs() {
   static bool done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (done[dev]) return cudaSuccess;
-  const int bytes = (int)K1Stage<PPT>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_k1<PPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_k1<PPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k1_smem<PPT>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_k1<PPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    e = cudaFuncSetAttribute(k_k1<PPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k1_smem<PPT>());
   if (e == cudaSuccess) done[dev] = true;
   return e;
 }
@@ -1079,11 +1228,16 @@ template <int PPT>
 static cudaError_t launch_k1_ppt(const Work& w, int level, int grid, cudaStream_t st) {
   cudaError_t e = k1_attrs<PPT>();
   if (e != cudaSuccess) return e;
-  const size_t bytes = K1Stage<PPT>::bytes;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kK1Threads);
+  cfg.dynamicSmemBytes = k1_smem<PPT>();
+  cfg.stream = st;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
   count_launch();
-  if (level == 0) k_k1<PPT, true><<<grid, kK1Threads, bytes, st>>>(w, level);
-  else k_k1<PPT, false><<<grid, kK1Threads, bytes, st>>>(w, level);
-  return cudaGetLastError();
+  if (level == 0) return cudaLaunchKernelEx(&cfg, k_k1<PPT, true>, w, level);
+  return cudaLaunchKernelEx(&cfg, k_k1<PPT, false>, w, level);
 }
 
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st) {
@@ -1097,11 +1251,10 @@ cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t 
 
 template <int PPT>
 static int k1_occ() {
-  if (k1_attrs<PPT>() != cudaSuccess) return 1;
   int n = 0, n0 = 0;
-  const size_t bytes = K1Stage<PPT>::bytes;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_k1<PPT, false>, kK1Threads, bytes) != cudaSuccess) return 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_k1<PPT, true>, kK1Threads, bytes) != cudaSuccess) return 1;
+  if (k1_attrs<PPT>() != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_k1<PPT, false>, kK1Threads, k1_smem<PPT>()) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_k1<PPT, true>, kK1Threads, k1_smem<PPT>()) != cudaSuccess) return 1;
   n = n0 < n ? n0 : n;
   return n > 0 ? n : 1;
 }
@@ -1121,7 +1274,7 @@ cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int k3_smem_bytes() { return (int)(((size_t)kK3Cap * 24 + sizeof(Frame) * kK3Stack) * kK3Warps); }
+int k3_smem_bytes() { return (int)(kK3PerWarp * kK3Warps); }
 
 cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st) {
   static bool attr[64] = {};

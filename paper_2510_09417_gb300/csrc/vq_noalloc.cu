@@ -37,7 +37,6 @@ struct DeviceState {
   bool ready = false;
   unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
   int sms = 0;
-  int k1_bps = 0;
 };
 
 std::mutex g_mu;
@@ -70,7 +69,7 @@ size_t carve(Work& w, unsigned char* base, long long n, long long** scan_tmp) {
   w.capT0 = (int)(n / kK0Tile + nsets + 1);
   w.k0part = reinterpret_cast<K0Part*>(take(sizeof(K0Part) * w.capT0));
   w.small_max = kNoAllocSmallMax;
-  w.tile = kK1Threads * kNoAllocPPT;
+  w.tile = kK1Threads * kNoAllocPPT;  // partition block tile: 256 threads x ppt points
   w.capS = (int)(n / (kNoAllocSmallMax + 1) + 2);
   w.capT = (int)(n / w.tile + w.capS + 1);
   w.capQ = 2 * w.capS + nsets + 16;
@@ -79,7 +78,8 @@ size_t carve(Work& w, unsigned char* base, long long n, long long** scan_tmp) {
     w.geom[b] = reinterpret_cast<SegGeom*>(take(sizeof(SegGeom) * w.capS));
     w.tile_seg[b] = reinterpret_cast<int*>(take(sizeof(int) * w.capT));
     w.status[b] = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * w.capT));
-    w.cand[b] = reinterpret_cast<TileCand*>(take(sizeof(TileCand) * w.capT));
+    w.cand[b] = reinterpret_cast<TileRec*>(take(sizeof(TileRec) * w.capT));
+    w.sstate[b] = reinterpret_cast<SegState*>(take(sizeof(SegState) * w.capS));
   }
   w.k3q = reinterpret_cast<SegRec*>(take(sizeof(SegRec) * w.capQ));
   w.ctrl = reinterpret_cast<Ctrl*>(take(sizeof(Ctrl)));
@@ -103,7 +103,6 @@ vq_status setup(int dev, DeviceState& d) {
     return VQ_ERR_CUDA;
   }
   if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return VQ_ERR_CUDA;
-  d.k1_bps = k1_blocks_per_sm(kNoAllocPPT);
   d.scratch = static_cast<unsigned char*>(p);
   d.ready = true;
   return VQ_OK;
@@ -143,6 +142,7 @@ extern "C" vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t
   w.N = (int)n;
   w.timeout_ns = kNoAllocTimeoutNs;
   w.drop_tile = -1;
+  w.ordered = 0;
 
 #define NA_CHECK(call)                                     \
   do {                                                     \
@@ -161,15 +161,17 @@ extern "C" vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t
   NA_CHECK(scan_exclusive_i32(w.k0_tile_start, 2, reinterpret_cast<int*>(scan_tmp), st));
   NA_CHECK(launch_k0(w, d.sms * 8, st));
   NA_CHECK(launch_k0_finalize(w, st));
+  long long k1_grid = n / w.tile + 2;  // level 0: at most this many tiles
   for (int level = 0;; level++) {
     NA_CHECK(launch_prologue(w, level, st));
-    NA_CHECK(launch_k1(w, level, kNoAllocPPT, d.sms * d.k1_bps, st));
+    if (k1_grid > 0) NA_CHECK(launch_k1(w, level, kNoAllocPPT, (int)k1_grid, st));
     NA_CHECK(launch_k2(w, level, d.sms * 8, st));
     NA_CHECK(launch_k3(w, d.sms * 2, st));
     NA_CHECK(cudaMemcpyAsync(&g_ctrl_host, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     NA_CHECK(cudaStreamSynchronize(st));
     if (g_ctrl_host.err & kErrFatal) break;
     if (g_ctrl_host.k1_segs[(level + 1) & 1] == 0) break;
+    k1_grid = g_ctrl_host.k1_tiles[(level + 1) & 1];
     if (level > n + 1) {
       g_ctrl_host.err |= kErrInternal;
       break;

@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("timeout_ns", ctypes.c_int64),
         ("debug_drop_tile", ctypes.c_int32),
-        ("reserved1", ctypes.c_int32),
+        ("ordered", ctypes.c_int32),
     ]
 
 

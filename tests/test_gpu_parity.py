@@ -157,12 +157,22 @@ def test_lookback_timeout_is_reported(vq):
     bounded waits expire; the call reports VQ_ERR_TIMEOUT and the device
     stays usable."""
     x, y = synth.points("square", 400_000, 3)
-    vq.vq_set_config(debug_drop_tile=2, timeout_ns=20_000_000)
+    vq.vq_set_config(ordered=1, debug_drop_tile=2, timeout_ns=20_000_000)
     with pytest.raises(vq.VQError) as e:
         gpu_hull(vq, x, y)
     assert e.value.status == -6
     vq.vq_set_config(debug_drop_tile=-1, timeout_ns=2_000_000_000)
     check(vq, x, y)
+
+
+@pytest.mark.parametrize("ppt", [4, 8, 16])
+def test_ordered_mode(vq, ppt):
+    """Offsets by decoupled look-back (stable partition) give the same hull
+    and per-level counts as the default atomic offsets."""
+    vq.vq_set_config(ordered=1, points_per_thread=ppt)
+    for dist, n in (("disk", 300_000), ("circle", 120_000), ("square", 1_000_000), ("kuzmin", 200_000)):
+        x, y = synth.points(dist, n, 17)
+        check(vq, x, y, stats=True)
 
 
 @pytest.mark.parametrize("ppt", [4, 8, 16])
