@@ -733,6 +733,8 @@ __global__ void __launch_bounds__(kK1Threads) k_k1(Work w, int level) {
   }
 }
 
+#include "vq_partition.cuh"
+
 // ---------------------------------------------------------------------------
 // K2: per segment, cross-tile argmax, emission, children
 // ---------------------------------------------------------------------------
@@ -1240,7 +1242,81 @@ static cudaError_t launch_k1_ppt(const Work& w, int level, int grid, cudaStream_
   return cudaLaunchKernelEx(&cfg, k_k1<PPT, false>, w, level);
 }
 
+// Streaming partition kernel (vq_partition.cuh): 4 consumer warps and one
+// producer warp per CTA; the stage count fills shared memory for 2-4 CTAs
+// per SM.  The tile (32 * 4 * ppt points) matches the look-back kernel's.
+template <int PPT>
+struct K1SCfg;
+template <>
+struct K1SCfg<4> { static constexpr int NS = 4, MINB = 4; };
+template <>
+struct K1SCfg<8> { static constexpr int NS = 3, MINB = 3; };
+template <>
+struct K1SCfg<16> { static constexpr int NS = 2, MINB = 2; };
+
+static int device_sms() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (sms[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+    sms[dev] = n;
+  }
+  return sms[dev];
+}
+
+template <int PPT>
+static int k1s_blocks_per_sm() {
+  constexpr int NS = K1SCfg<PPT>::NS;
+  typedef K1S<PPT, 4, NS> C;
+  static int occ[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+  if (occ[dev] > 0) return occ[dev];
+  if (cudaFuncSetAttribute(k_k1s<PPT, 4, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_k1s<PPT, 4, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) !=
+          cudaSuccess)
+    return -1;
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_k1s<PPT, 4, NS, true>, C::NT + 32, C::smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_k1s<PPT, 4, NS, false>, C::NT + 32, C::smem) !=
+          cudaSuccess)
+    return -1;
+  const int n = a < b ? a : b;
+  occ[dev] = n > 0 ? n : 1;
+  return occ[dev];
+}
+
+template <int PPT>
+static cudaError_t launch_k1s_ppt(const Work& w, int level, int tiles, cudaStream_t st) {
+  constexpr int NS = K1SCfg<PPT>::NS;
+  typedef K1S<PPT, 4, NS> C;
+  static_assert(C::TB == kK1Threads * PPT, "tile sizes of the two partition kernels agree");
+  const int occ = k1s_blocks_per_sm<PPT>();
+  if (occ < 0) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)occ * device_sms();
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  count_launch();
+  if (level == 0)
+    k_k1s<PPT, 4, NS, true><<<(unsigned)grid, C::NT + 32, C::smem, st>>>(w, level);
+  else
+    k_k1s<PPT, 4, NS, false><<<(unsigned)grid, C::NT + 32, C::smem, st>>>(w, level);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st) {
+  if (!w.ordered) {
+    switch (ppt) {
+      case 4: return launch_k1s_ppt<4>(w, level, grid, st);
+      case 8: return launch_k1s_ppt<8>(w, level, grid, st);
+      case 16: return launch_k1s_ppt<16>(w, level, grid, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (ppt) {
     case 4: return launch_k1_ppt<4>(w, level, grid, st);
     case 8: return launch_k1_ppt<8>(w, level, grid, st);
