@@ -142,9 +142,11 @@ static size_t layout(Work& w, char* base, long long N, int nsets, long long nkey
   };
   const long long n = N > 0 ? N : 1;
   for (int b = 0; b < 2; b++) {
-    w.bx[b] = reinterpret_cast<double*>(take(sizeof(double) * n));
-    w.by[b] = reinterpret_cast<double*>(take(sizeof(double) * n));
-    w.bi[b] = reinterpret_cast<int*>(take(sizeof(int) * n));
+    // 16 bytes of padding: the partition kernel's bulk copies may read up
+    // to 15 bytes past a tile's last point
+    w.bx[b] = reinterpret_cast<double*>(take(sizeof(double) * n + 16));
+    w.by[b] = reinterpret_cast<double*>(take(sizeof(double) * n + 16));
+    w.bi[b] = reinterpret_cast<int*>(take(sizeof(int) * n + 16));
   }
   w.nkeys = nkeys;
   w.slot = reinterpret_cast<int*>(take(sizeof(int) * (nkeys + 1)));
@@ -154,14 +156,18 @@ static size_t layout(Work& w, char* base, long long N, int nsets, long long nkey
   w.capT0 = (int)(n / kK0Tile + nsets + 1);
   w.k0part = reinterpret_cast<K0Part*>(take(sizeof(K0Part) * w.capT0));
   w.small_max = cfg.small_max;
-  w.tile = kK1Threads * cfg.ppt;  // partition block tile: 256 threads x ppt points
+  // partition tile: one warp's (32 x ppt points), or one look-back block's
+  w.tile = (cfg.ordered ? kK1Threads : kWarp) * cfg.ppt;
   w.capS = (int)(n / (cfg.small_max + 1) + 2);
   w.capT = (int)(n / w.tile + w.capS + 1);
   w.capQ = 2 * w.capS + nsets + 16;
+  w.capJ = w.capT / kFillTiles + w.capS + 1;
   for (int b = 0; b < 2; b++) {
     w.segs[b] = reinterpret_cast<SegRec*>(take(sizeof(SegRec) * w.capS));
     w.geom[b] = reinterpret_cast<SegGeom*>(take(sizeof(SegGeom) * w.capS));
     w.tile_seg[b] = reinterpret_cast<int*>(take(sizeof(int) * w.capT));
+    w.tdesc[b] = reinterpret_cast<TileDesc*>(take(sizeof(TileDesc) * w.capT));
+    w.fjobs[b] = reinterpret_cast<int4*>(take(sizeof(int4) * w.capJ));
     w.status[b] = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * w.capT));
     w.cand[b] = reinterpret_cast<TileRec*>(take(sizeof(TileRec) * w.capT));
     w.sstate[b] = reinterpret_cast<SegState*>(take(sizeof(SegState) * w.capS));
@@ -252,6 +258,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   VQ_CHECK(tm.begin(kKindK0));
   VQ_CHECK(launch_k0(w, c.sms * 8, st));
   VQ_CHECK(launch_k0_finalize(w, st));
+  VQ_CHECK(launch_tilemap(w, 0, c.sms * 4, st));
   VQ_CHECK(tm.end());
 
   int level = 0;
@@ -264,6 +271,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
     if (k1_grid > 0) VQ_TIMED(tm, kKindK1, launch_k1(w, level, cfg.ppt, (int)k1_grid, st));
     c.prof.k1_launches++;
     VQ_TIMED(tm, kKindK2, launch_k2(w, level, c.sms * 8, st));
+    VQ_TIMED(tm, kKindK2, launch_tilemap(w, (level + 1) & 1, c.sms * 4, st));
     VQ_TIMED(tm, kKindK3, launch_k3(w, c.sms * 2, st));
     VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     VQ_CHECK(cudaStreamSynchronize(st));
@@ -287,6 +295,15 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   c.prof.k1_points_read += c.h_ctrl->k1_read;
   c.prof.k1_points_kept += c.h_ctrl->k1_kept;
   const unsigned err = c.h_ctrl->err;
+#ifdef VQ_K1_PROFILE
+  {
+    const unsigned long long* q = c.h_ctrl->k1prof;
+    fprintf(stderr,
+            "vqhull k1prof tiles=%llu wait=%llu classify=%llu farthest=%llu atomic=%llu store=%llu issue=%llu "
+            "total=%llu far_bounds=%llu far_searches=%llu multi_lane=%llu cands=%llu\n",
+            q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8], q[9], q[10], q[11]);
+  }
+#endif
   if (c.h_ctrl->dbg_site)
     fprintf(stderr, "vqhull: bounds check %d failed (value %lld), level loop ran %d levels\n", c.h_ctrl->dbg_site,
             c.h_ctrl->dbg_val, levels_run);

@@ -65,8 +65,9 @@ struct Ctrl {
   long long k1_read;        // points classified by the partition kernel
   long long k1_kept;        // of those, points written to a child
   int dbg_site;             // checked builds: first failed bounds check
-  int dbg_pad;
+  int fill_jobs[2];         // tile-map fill jobs per level parity
   long long dbg_val;        // checked builds: the offending value
+  unsigned long long k1prof[12];  // profiling builds: partition-kernel cycle and event counters
 };
 
 // A live segment: points off .. off+len-1 of its source buffer, hull edge
@@ -118,6 +119,17 @@ struct BestRec {
 struct TileRec {
   BestRec own[2];
   BestRec incl[2];
+};
+
+// Where a partition tile's points are: written per tile when the tile map is
+// built, read (one 32-byte load) by the partition kernel's copy issuer.
+struct alignas(16) TileDesc {
+  int sid;    // segment
+  int begin;  // first buffer position of the tile
+  int count;  // points in the tile
+  int flags;  // segment flags
+  int off, len;  // segment range
+  int pad0, pad1;
 };
 
 // Per big segment and level: output cursors and farthest-point candidates.
@@ -208,6 +220,27 @@ __device__ __forceinline__ float trunc_f32(double v) {
   const unsigned f = __funnelshift_l(lo, mag, 3) - 0xC0000000u;  // (1023 - 127) << 23, mod 2^32
   return __uint_as_float(f | (hi & 0x80000000u));
 }
+
+// Exact FP32 -> FP64 widening by integer operations (GB300's FP64 pipe is
+// narrow; per-tile bookkeeping stays off it).  Normal numbers rebias the
+// exponent by 1023 - 127; subnormals m * 2^-149 are renormalised at their
+// leading bit; zeros, infinities and NaNs keep their class.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned long long b;
+  if (e == 0xffu) b = 0x7ff0000000000000ull | ((unsigned long long)m << 29);
+  else if (e != 0u) b = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  else if (m == 0u) b = 0ull;
+  else {
+    const int p = 31 - __clz(m);
+    b = ((unsigned long long)(p + 874) << 52) | ((unsigned long long)(m - (1u << p)) << (52 - p));
+  }
+  return __longlong_as_double((long long)(s | b));
+}
+__device__ __forceinline__ double widen(float v) { return f2d_exact(v); }
+__device__ __forceinline__ double widen(double v) { return v; }
 
 // ---------------------------------------------------------------------------
 // Tier 1: FP32 orient with a rigorous error bound.

@@ -15,6 +15,7 @@ constexpr int kK3Cap = 1024;        // points per warp in the small-segment kern
 constexpr int kK3Warps = 4;
 constexpr int kK3Stack = 24;
 constexpr int kK4Words = 1024;      // bitmap words per ordering block (256 threads x 4)
+constexpr int kFillTiles = 1024;    // tiles per tile-map fill job
 
 // Everything a kernel needs, passed by value.
 struct Work {
@@ -37,15 +38,17 @@ struct Work {
   SegRec* segs[2];
   SegGeom* geom[2];
   int* tile_seg[2];
+  TileDesc* tdesc[2];        // per tile: where its points are
+  int4* fjobs[2];            // tile-map fill jobs: {segment, first tile, tiles, 0}
   unsigned long long* status[2];
   TileRec* cand[2];
   SegState* sstate[2];       // per big segment: cursors and farthest-point candidates
   SegRec* k3q;
   Ctrl* ctrl;
   long long* stats;          // [3][kMaxLevels]: points read, points kept, segments
-  int capS, capT, capQ, capT0;
+  int capS, capT, capQ, capT0, capJ;
   int small_max;             // segments with len <= small_max go to the small kernel
-  int tile;                  // K1 tile size
+  int tile;                  // K1 tile size (points)
   long long timeout_ns;
   int drop_tile;             // test knob: this K1 tile never publishes (-1: none)
   int ordered;               // 1: offsets by decoupled look-back (stable layout); 0: atomic cursors
@@ -58,6 +61,7 @@ cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st);
 cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st);
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st);
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st);
+cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st);
 cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long long* total,
                          long long* tmp, cudaStream_t st);

@@ -79,16 +79,22 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 
 // Append a segment for the partition kernel (whole warp): reserve its tiles,
 // write its geometry and the tile -> segment map, clear the tiles' status.
+// Register a big segment for the next partition level: a slot, a range of
+// tiles, its geometry and its zeroed cursor; the per-tile map is written by
+// k_tilemap from fill jobs of at most kFillTiles tiles each.
 __device__ void push_k1_warp(const Work& w, int par, SegRec R, int lane) {
-  const int ntiles = (R.len + w.tile - 1) / w.tile;  // w.tile = 32 * points per lane
-  int slot = 0, base = 0;
+  const int ntiles = (R.len + w.tile - 1) / w.tile;
+  const int njobs = (ntiles + kFillTiles - 1) / kFillTiles;
+  int slot = 0, base = 0, job = 0;
   if (lane == 0) {
     slot = atomicAdd(&w.ctrl->k1_segs[par], 1);
     base = atomicAdd(&w.ctrl->k1_tiles[par], ntiles);
+    job = atomicAdd(&w.ctrl->fill_jobs[par], njobs);
   }
   slot = __shfl_sync(kFull, slot, 0);
   base = __shfl_sync(kFull, base, 0);
-  if (slot >= w.capS || base > w.capT - ntiles) {
+  job = __shfl_sync(kFull, job, 0);
+  if (slot >= w.capS || base > w.capT - ntiles || job > w.capJ - njobs) {
     if (lane == 0) atomicOr(&w.ctrl->err, kErrCapacity);
     return;
   }
@@ -103,12 +109,38 @@ __device__ void push_k1_warp(const Work& w, int par, SegRec R, int lane) {
     fill_geom(g, w.x[R.a], w.y[R.a], w.x[R.b], w.y[R.b], w.x[R.r], w.y[R.r]);
     w.geom[par][slot] = g;
   }
-  for (int i = lane; i < ntiles; i += kWarp) {
-    w.tile_seg[par][base + i] = slot;
-    w.status[par][base + i] = 0ull;
-  }
+  for (int i = lane; i < njobs; i += kWarp)
+    w.fjobs[par][job + i] = make_int4(slot, base + i * kFillTiles, min(kFillTiles, ntiles - i * kFillTiles), 0);
   int* st = reinterpret_cast<int*>(&w.sstate[par][slot]);
   for (int i = lane; i < (int)(sizeof(SegState) / sizeof(int)); i += kWarp) st[i] = 0;
+}
+
+// The per-tile map of level parity `par`: segment, look-back status word
+// and the partition kernel's tile descriptor, one fill job per block.
+__global__ void __launch_bounds__(256) k_tilemap(Work w, int par) {
+  if (fatal(w)) return;
+  const int njobs = min(*reinterpret_cast<volatile int*>(&w.ctrl->fill_jobs[par]), w.capJ);
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const int4 J = w.fjobs[par][j];
+    const SegRec S = w.segs[par][J.x];
+    for (int i = threadIdx.x; i < J.z; i += blockDim.x) {
+      const int t = J.y + i;
+      const int k = t - S.tile_base;
+      if (!VQ_OK_IDX(w, 45, t, 0, w.capT)) break;
+      w.tile_seg[par][t] = J.x;
+      if (w.ordered) w.status[par][t] = 0ull;
+      TileDesc d;
+      d.sid = J.x;
+      d.begin = S.off + k * w.tile;
+      d.count = min(w.tile, S.len - k * w.tile);
+      d.flags = S.flags;
+      d.off = S.off;
+      d.len = S.len;
+      d.pad0 = 0;
+      d.pad1 = 0;
+      w.tdesc[par][t] = d;
+    }
+  }
 }
 
 __device__ __forceinline__ void push_k3(const Work& w, const SegRec& R) {
@@ -296,6 +328,7 @@ __global__ void k_prologue(Work w, int level) {
   w.ctrl->k1_ticket = 0;
   w.ctrl->k1_segs[par ^ 1] = 0;
   w.ctrl->k1_tiles[par ^ 1] = 0;
+  w.ctrl->fill_jobs[par ^ 1] = 0;
   if (level > 0) w.ctrl->k3_count = 0;
   w.ctrl->level = level;
 }
@@ -318,7 +351,7 @@ __device__ __forceinline__ void take_best(CandT<K>& b, const double* L, double x
 template <typename K>
 __device__ __forceinline__ CandT<double> to_double(const CandT<K>& c) {
   CandT<double> d;
-  d.x = c.x; d.y = c.y; d.lo = (double)c.lo; d.hi = (double)c.hi; d.idx = c.idx;
+  d.x = c.x; d.y = c.y; d.lo = widen(c.lo); d.hi = widen(c.hi); d.idx = c.idx;
   return d;
 }
 
@@ -1228,6 +1261,7 @@ static cudaError_t k1_attrs() {
 
 template <int PPT>
 static cudaError_t launch_k1_ppt(const Work& w, int level, int grid, cudaStream_t st) {
+  if (w.tile != kK1Threads * PPT) return cudaErrorInvalidValue;
   cudaError_t e = k1_attrs<PPT>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1242,17 +1276,16 @@ static cudaError_t launch_k1_ppt(const Work& w, int level, int grid, cudaStream_
   return cudaLaunchKernelEx(&cfg, k_k1<PPT, false>, w, level);
 }
 
-// Streaming partition kernel (vq_partition.cuh): 4 consumer warps and one
-// producer warp per CTA; the stage count fills shared memory for 2-4 CTAs
-// per SM.  The tile (32 * 4 * ppt points) matches the look-back kernel's.
+// Streaming partition kernel (vq_partition.cuh): independent warps, each
+// with a ring of NS stages of 32 * ppt points; WPB warps per block.
 template <int PPT>
-struct K1SCfg;
+struct K1WCfg;
 template <>
-struct K1SCfg<4> { static constexpr int NS = 4, MINB = 4; };
+struct K1WCfg<4> { static constexpr int WPB = 4, NS = 4; };
 template <>
-struct K1SCfg<8> { static constexpr int NS = 3, MINB = 3; };
+struct K1WCfg<8> { static constexpr int WPB = 4, NS = 3; };
 template <>
-struct K1SCfg<16> { static constexpr int NS = 2, MINB = 2; };
+struct K1WCfg<16> { static constexpr int WPB = 4, NS = 2; };
 
 static int device_sms() {
   static int sms[64] = {};
@@ -1267,22 +1300,22 @@ static int device_sms() {
 }
 
 template <int PPT>
-static int k1s_blocks_per_sm() {
-  constexpr int NS = K1SCfg<PPT>::NS;
-  typedef K1S<PPT, 4, NS> C;
+static int k1w_blocks_per_sm() {
+  constexpr int WPB = K1WCfg<PPT>::WPB, NS = K1WCfg<PPT>::NS;
+  typedef K1W<PPT, WPB, NS> C;
   static int occ[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
   if (occ[dev] > 0) return occ[dev];
-  if (cudaFuncSetAttribute(k_k1s<PPT, 4, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) !=
+  if (cudaFuncSetAttribute(k_k1w<PPT, WPB, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_k1s<PPT, 4, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) !=
+      cudaFuncSetAttribute(k_k1w<PPT, WPB, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) !=
           cudaSuccess)
     return -1;
   int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_k1s<PPT, 4, NS, true>, C::NT + 32, C::smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_k1w<PPT, WPB, NS, true>, 32 * WPB, C::smem) !=
           cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_k1s<PPT, 4, NS, false>, C::NT + 32, C::smem) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_k1w<PPT, WPB, NS, false>, 32 * WPB, C::smem) !=
           cudaSuccess)
     return -1;
   const int n = a < b ? a : b;
@@ -1291,29 +1324,30 @@ static int k1s_blocks_per_sm() {
 }
 
 template <int PPT>
-static cudaError_t launch_k1s_ppt(const Work& w, int level, int tiles, cudaStream_t st) {
-  constexpr int NS = K1SCfg<PPT>::NS;
-  typedef K1S<PPT, 4, NS> C;
-  static_assert(C::TB == kK1Threads * PPT, "tile sizes of the two partition kernels agree");
-  const int occ = k1s_blocks_per_sm<PPT>();
+static cudaError_t launch_k1w_ppt(const Work& w, int level, int tiles, cudaStream_t st) {
+  constexpr int WPB = K1WCfg<PPT>::WPB, NS = K1WCfg<PPT>::NS;
+  typedef K1W<PPT, WPB, NS> C;
+  if (w.tile != C::TW) return cudaErrorInvalidValue;
+  const int occ = k1w_blocks_per_sm<PPT>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   long long grid = (long long)occ * device_sms();
-  if (grid > tiles) grid = tiles;
+  const long long need = ((long long)tiles + WPB - 1) / WPB;
+  if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   count_launch();
   if (level == 0)
-    k_k1s<PPT, 4, NS, true><<<(unsigned)grid, C::NT + 32, C::smem, st>>>(w, level);
+    k_k1w<PPT, WPB, NS, true><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
   else
-    k_k1s<PPT, 4, NS, false><<<(unsigned)grid, C::NT + 32, C::smem, st>>>(w, level);
+    k_k1w<PPT, WPB, NS, false><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
   return cudaGetLastError();
 }
 
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st) {
   if (!w.ordered) {
     switch (ppt) {
-      case 4: return launch_k1s_ppt<4>(w, level, grid, st);
-      case 8: return launch_k1s_ppt<8>(w, level, grid, st);
-      case 16: return launch_k1s_ppt<16>(w, level, grid, st);
+      case 4: return launch_k1w_ppt<4>(w, level, grid, st);
+      case 8: return launch_k1w_ppt<8>(w, level, grid, st);
+      case 16: return launch_k1w_ppt<16>(w, level, grid, st);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -1347,6 +1381,12 @@ int k1_blocks_per_sm(int ppt) {
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st) {
   count_launch();
   k_k2<<<grid, 256, 0, st>>>(w, level);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st) {
+  count_launch();
+  k_tilemap<<<grid, 256, 0, st>>>(w, par);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ namespace {
 
 constexpr long long kNoAllocMaxPoints = 1ll << 20;
 constexpr size_t kNoAllocBytes = 64ull << 20;
-constexpr int kNoAllocPPT = 8;           // partition tile: 256 threads x 8 points
+constexpr int kNoAllocPPT = 8;           // partition tile: 32 lanes x 8 points
 constexpr int kNoAllocSmallMax = 1024;   // small-segment threshold
 constexpr long long kNoAllocTimeoutNs = 2000000000ll;
 
@@ -57,9 +57,9 @@ size_t carve(Work& w, unsigned char* base, long long n, long long** scan_tmp) {
   const int nsets = 1;
   const long long nkeys = n + nsets;
   for (int b = 0; b < 2; b++) {
-    w.bx[b] = reinterpret_cast<double*>(take(sizeof(double) * n));
-    w.by[b] = reinterpret_cast<double*>(take(sizeof(double) * n));
-    w.bi[b] = reinterpret_cast<int*>(take(sizeof(int) * n));
+    w.bx[b] = reinterpret_cast<double*>(take(sizeof(double) * n + 16));  // 16-byte tail pad for bulk copies
+    w.by[b] = reinterpret_cast<double*>(take(sizeof(double) * n + 16));
+    w.bi[b] = reinterpret_cast<int*>(take(sizeof(int) * n + 16));
   }
   w.nkeys = nkeys;
   w.slot = reinterpret_cast<int*>(take(sizeof(int) * (nkeys + 1)));
@@ -69,14 +69,17 @@ size_t carve(Work& w, unsigned char* base, long long n, long long** scan_tmp) {
   w.capT0 = (int)(n / kK0Tile + nsets + 1);
   w.k0part = reinterpret_cast<K0Part*>(take(sizeof(K0Part) * w.capT0));
   w.small_max = kNoAllocSmallMax;
-  w.tile = kK1Threads * kNoAllocPPT;  // partition block tile: 256 threads x ppt points
+  w.tile = kWarp * kNoAllocPPT;  // partition tile: one warp's points
   w.capS = (int)(n / (kNoAllocSmallMax + 1) + 2);
   w.capT = (int)(n / w.tile + w.capS + 1);
   w.capQ = 2 * w.capS + nsets + 16;
+  w.capJ = w.capT / kFillTiles + w.capS + 1;
   for (int b = 0; b < 2; b++) {
     w.segs[b] = reinterpret_cast<SegRec*>(take(sizeof(SegRec) * w.capS));
     w.geom[b] = reinterpret_cast<SegGeom*>(take(sizeof(SegGeom) * w.capS));
     w.tile_seg[b] = reinterpret_cast<int*>(take(sizeof(int) * w.capT));
+    w.tdesc[b] = reinterpret_cast<TileDesc*>(take(sizeof(TileDesc) * w.capT));
+    w.fjobs[b] = reinterpret_cast<int4*>(take(sizeof(int4) * w.capJ));
     w.status[b] = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * w.capT));
     w.cand[b] = reinterpret_cast<TileRec*>(take(sizeof(TileRec) * w.capT));
     w.sstate[b] = reinterpret_cast<SegState*>(take(sizeof(SegState) * w.capS));
@@ -161,11 +164,13 @@ extern "C" vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t
   NA_CHECK(scan_exclusive_i32(w.k0_tile_start, 2, reinterpret_cast<int*>(scan_tmp), st));
   NA_CHECK(launch_k0(w, d.sms * 8, st));
   NA_CHECK(launch_k0_finalize(w, st));
+  NA_CHECK(launch_tilemap(w, 0, d.sms * 4, st));
   long long k1_grid = n / w.tile + 2;  // level 0: at most this many tiles
   for (int level = 0;; level++) {
     NA_CHECK(launch_prologue(w, level, st));
     if (k1_grid > 0) NA_CHECK(launch_k1(w, level, kNoAllocPPT, (int)k1_grid, st));
     NA_CHECK(launch_k2(w, level, d.sms * 8, st));
+    NA_CHECK(launch_tilemap(w, (level + 1) & 1, d.sms * 4, st));
     NA_CHECK(launch_k3(w, d.sms * 2, st));
     NA_CHECK(cudaMemcpyAsync(&g_ctrl_host, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     NA_CHECK(cudaStreamSynchronize(st));

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libvqhull.so")
 STAMP = os.path.join(BUILD, "lib.arch")
 SOURCES = ["vq_kernels.cu", "vq_api.cu", "vq_server.cu", "vq_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, h) for h in ("vq_device.cuh", "vq_internal.h")] + [
+HEADERS = [os.path.join(CSRC, h) for h in ("vq_device.cuh", "vq_internal.h", "vq_partition.cuh")] + [
     os.path.join(ROOT, "include", "vqhull.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -25,6 +25,10 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 CHECKED = os.environ.get("VQ_CHECKED", "") == "1"
 if CHECKED:
     FLAGS = FLAGS + ["-DVQ_CHECKED=1"]
+# VQ_K1_PROFILE=1 adds per-phase cycle counters to the partition kernel,
+# printed to stderr after each call (profiling aid; off by default)
+if os.environ.get("VQ_K1_PROFILE", "") == "1":
+    FLAGS = FLAGS + ["-DVQ_K1_PROFILE=1"]
 _lock = threading.Lock()
 
 
