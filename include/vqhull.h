@@ -130,10 +130,11 @@ vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t n, int32_t
 
 /* Tuning knobs (process-wide; take effect on the next call). */
 typedef struct {
-  int32_t points_per_thread; /* partition kernel: 4, 8 or 16 points per thread */
+  int32_t points_per_thread; /* partition kernel: 4, 8 or 16 points per lane
+                                (default 16: a warp tile of 512 points)      */
   int32_t small_max;         /* segments of <= small_max points (2..1024) are
                                 finished by the shared-memory kernel          */
-  int32_t k1_blocks_per_sm;  /* reserved (partition blocks are one per tile)  */
+  int32_t k1_blocks_per_sm;  /* reserved                                     */
   int32_t profile;           /* 1: time every kernel with CUDA events (see
                                 vq_profile_read); 0: off                     */
   int64_t timeout_ns;        /* bound of every device-side wait              */

@@ -17,7 +17,7 @@
 namespace vq {
 
 struct Config {
-  int ppt = 8;
+  int ppt = 16;
   int small_max = 1024;
   int k1_bps = 0;
   int profile = 0;
@@ -260,6 +260,10 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   VQ_CHECK(launch_k0_finalize(w, st));
   VQ_CHECK(launch_tilemap(w, 0, c.sms * 4, st));
   VQ_CHECK(tm.end());
+  // which partition kernel: FP32-only unless some set needs the FP64 tier
+  VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  VQ_CHECK(cudaStreamSynchronize(st));
+  w.all_fast = c.h_ctrl->any_slow ? 0 : 1;
 
   int level = 0;
   int levels_run = 0;

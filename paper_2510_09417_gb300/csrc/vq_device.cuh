@@ -66,6 +66,8 @@ struct Ctrl {
   long long k1_kept;        // of those, points written to a child
   int dbg_site;             // checked builds: first failed bounds check
   int fill_jobs[2];         // tile-map fill jobs per level parity
+  int any_slow;             // some point set needs the FP64 tier (|coordinate| >= 2^40)
+  int pad0;
   long long dbg_val;        // checked builds: the offending value
   unsigned long long k1prof[12];  // profiling builds: partition-kernel cycle and event counters
 };

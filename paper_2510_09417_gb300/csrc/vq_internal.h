@@ -52,6 +52,7 @@ struct Work {
   long long timeout_ns;
   int drop_tile;             // test knob: this K1 tile never publishes (-1: none)
   int ordered;               // 1: offsets by decoupled look-back (stable layout); 0: atomic cursors
+  int all_fast;              // host's copy of !Ctrl::any_slow: selects the FP32-only partition kernel
 };
 
 // launchers (vq_kernels.cu); all enqueue on `st`

@@ -298,6 +298,7 @@ __global__ void k_k0_finalize(Work w) {
     S.p = p;
     S.q = q;
     S.flags = (fl & 2) ? 0 : kSegFast;
+    if ((fl & 2) && lane == 0) atomicOr(&w.ctrl->any_slow, 1);
     if (lane == 0) {
       w.sets[s] = S;
       emit(w, (long long)S.off + S.shift, p - S.off);
@@ -1299,7 +1300,7 @@ static int device_sms() {
   return sms[dev];
 }
 
-template <int PPT>
+template <int PPT, bool ALLFAST>
 static int k1w_blocks_per_sm() {
   constexpr int WPB = K1WCfg<PPT>::WPB, NS = K1WCfg<PPT>::NS;
   typedef K1W<PPT, WPB, NS> C;
@@ -1307,15 +1308,15 @@ static int k1w_blocks_per_sm() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
   if (occ[dev] > 0) return occ[dev];
-  if (cudaFuncSetAttribute(k_k1w<PPT, WPB, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_k1w<PPT, WPB, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) !=
-          cudaSuccess)
+  if (cudaFuncSetAttribute(k_k1w<PPT, WPB, NS, true, ALLFAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)C::smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_k1w<PPT, WPB, NS, false, ALLFAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)C::smem) != cudaSuccess)
     return -1;
   int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_k1w<PPT, WPB, NS, true>, 32 * WPB, C::smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_k1w<PPT, WPB, NS, true, ALLFAST>, 32 * WPB, C::smem) !=
           cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_k1w<PPT, WPB, NS, false>, 32 * WPB, C::smem) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_k1w<PPT, WPB, NS, false, ALLFAST>, 32 * WPB, C::smem) !=
           cudaSuccess)
     return -1;
   const int n = a < b ? a : b;
@@ -1323,12 +1324,12 @@ static int k1w_blocks_per_sm() {
   return occ[dev];
 }
 
-template <int PPT>
+template <int PPT, bool ALLFAST>
 static cudaError_t launch_k1w_ppt(const Work& w, int level, int tiles, cudaStream_t st) {
   constexpr int WPB = K1WCfg<PPT>::WPB, NS = K1WCfg<PPT>::NS;
   typedef K1W<PPT, WPB, NS> C;
   if (w.tile != C::TW) return cudaErrorInvalidValue;
-  const int occ = k1w_blocks_per_sm<PPT>();
+  const int occ = k1w_blocks_per_sm<PPT, ALLFAST>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   long long grid = (long long)occ * device_sms();
   const long long need = ((long long)tiles + WPB - 1) / WPB;
@@ -1336,18 +1337,23 @@ static cudaError_t launch_k1w_ppt(const Work& w, int level, int tiles, cudaStrea
   if (grid < 1) grid = 1;
   count_launch();
   if (level == 0)
-    k_k1w<PPT, WPB, NS, true><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
+    k_k1w<PPT, WPB, NS, true, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
   else
-    k_k1w<PPT, WPB, NS, false><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
+    k_k1w<PPT, WPB, NS, false, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
   return cudaGetLastError();
+}
+
+template <int PPT>
+static cudaError_t launch_k1w_sel(const Work& w, int level, int tiles, cudaStream_t st) {
+  return w.all_fast ? launch_k1w_ppt<PPT, true>(w, level, tiles, st) : launch_k1w_ppt<PPT, false>(w, level, tiles, st);
 }
 
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st) {
   if (!w.ordered) {
     switch (ppt) {
-      case 4: return launch_k1w_ppt<4>(w, level, grid, st);
-      case 8: return launch_k1w_ppt<8>(w, level, grid, st);
-      case 16: return launch_k1w_ppt<16>(w, level, grid, st);
+      case 4: return launch_k1w_sel<4>(w, level, grid, st);
+      case 8: return launch_k1w_sel<8>(w, level, grid, st);
+      case 16: return launch_k1w_sel<16>(w, level, grid, st);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -25,7 +25,7 @@ namespace {
 
 constexpr long long kNoAllocMaxPoints = 1ll << 20;
 constexpr size_t kNoAllocBytes = 64ull << 20;
-constexpr int kNoAllocPPT = 8;           // partition tile: 32 lanes x 8 points
+constexpr int kNoAllocPPT = 16;          // partition tile: 32 lanes x 16 points
 constexpr int kNoAllocSmallMax = 1024;   // small-segment threshold
 constexpr long long kNoAllocTimeoutNs = 2000000000ll;
 
@@ -165,6 +165,9 @@ extern "C" vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t
   NA_CHECK(launch_k0(w, d.sms * 8, st));
   NA_CHECK(launch_k0_finalize(w, st));
   NA_CHECK(launch_tilemap(w, 0, d.sms * 4, st));
+  NA_CHECK(cudaMemcpyAsync(&g_ctrl_host, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  NA_CHECK(cudaStreamSynchronize(st));
+  w.all_fast = g_ctrl_host.any_slow ? 0 : 1;
   long long k1_grid = n / w.tile + 2;  // level 0: at most this many tiles
   for (int level = 0;; level++) {
     NA_CHECK(launch_prologue(w, level, st));

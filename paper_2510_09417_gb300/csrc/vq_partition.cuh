@@ -100,14 +100,18 @@ struct alignas(16) K1Stage {
 static_assert(sizeof(SegGeom) == 96, "SegGeom is bulk-copied as 96 bytes");
 
 // A warp's private region: its stages, the upper bounds of its points'
-// keys (float or double, by the segment's tier) and the stages' mbarriers.
+// keys (FP32; FP64 bounds are rounded up, which only widens the candidate
+// filter) and the stages' mbarriers.
 template <int PPT, int NS>
 struct alignas(16) K1Ring {
   static constexpr int TW = 32 * PPT;
   K1Stage<TW> st[NS];
-  double hs[TW];
+  float hs[TW];
   unsigned long long full[NS];
 };
+
+__device__ __forceinline__ float hs_up(float v) { return v; }
+__device__ __forceinline__ float hs_up(double v) { return __double2float_ru(v); }
 
 // Pass-A classification.  FP32 tier: both lines are evaluated without
 // branches; 1 / 2 = left / right child, 0 = discard, 3 = undecided (the
@@ -302,7 +306,7 @@ __device__ __forceinline__ void k1w_flush(const Work& w, int par, K1Run& r, int 
 
 template <int PPT, bool SRC_INPUT, bool FAST>
 __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PPT>* __restrict__ sg,
-                                         unsigned char* hs_raw, int lane, K1Run& run,
+                                         float* __restrict__ hs, int lane, K1Run& run,
                                          unsigned long long* prof) {
   (void)prof;
   K1_MARK(c0);
@@ -315,7 +319,6 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
   const double* Y = sg->y + (sg->m.sy & 1);
   const int* I = sg->i + (sg->m.si & 3);
   const SegGeom* G = &sg->g;
-  K* hs = reinterpret_cast<K*>(hs_raw);
   SegState* ss = &w.sstate[par][sid];
   if (sid != run.sid) {
     k1w_flush(w, par, run, lane);
@@ -351,7 +354,7 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
       if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); h = hi; }
       if (c == 2) { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); h = hi; }
     }
-    hs[l] = h;
+    hs[l] = hs_up(h);
   }
   // exact tiers for the undecided points (rare)
   if (__any_sync(kFull, und != 0)) {
@@ -367,7 +370,7 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
         const K lo = key_lo(key, err), hi = key_hi(key, err);
         if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); }
         else { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); }
-        hs[l] = hi;
+        hs[l] = hs_up(hi);
       }
     }
   }
@@ -403,7 +406,7 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
     unsigned cm = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++)
-      if (((mc >> k) & 1u) && hs[k * kWarp + lane] >= thr) cm |= 1u << k;
+      if (((mc >> k) & 1u) && (K)hs[k * kWarp + lane] >= thr) cm |= 1u << k;
     const double* E = ch ? &G->rx : &G->ax;
     const unsigned lanes = __ballot_sync(kFull, cm != 0);
     if (lanes == 0) continue;
@@ -488,7 +491,9 @@ struct K1W {
 // Every warp takes a contiguous range of the level's tiles (consecutive
 // tiles mostly share a segment, so the running farthest points rarely
 // restart) and streams them through its ring.
-template <int PPT, int WPB, int NS, bool SRC_INPUT>
+// ALLFAST: every point set of the call is in the FP32 tier's range, so only
+// that path is compiled in (a smaller kernel).
+template <int PPT, int WPB, int NS, bool SRC_INPUT, bool ALLFAST>
 __global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Work w, int level) {
   typedef K1Ring<PPT, NS> Ring;
   extern __shared__ __align__(128) unsigned char k1w_smem[];
@@ -543,10 +548,10 @@ __global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Wor
       return;
     }
     K1Stage<32 * PPT>* sg = &R->st[s];
-    if (sg->m.flags & kSegFast)
-      k1w_tile<PPT, SRC_INPUT, true>(w, par, sg, reinterpret_cast<unsigned char*>(R->hs), lane, run, prof);
+    if (ALLFAST || (sg->m.flags & kSegFast))
+      k1w_tile<PPT, SRC_INPUT, true>(w, par, sg, R->hs, lane, run, prof);
     else
-      k1w_tile<PPT, SRC_INPUT, false>(w, par, sg, reinterpret_cast<unsigned char*>(R->hs), lane, run, prof);
+      k1w_tile<PPT, SRC_INPUT, ALLFAST>(w, par, sg, R->hs, lane, run, prof);
     __syncwarp();
     K1_MARK(i0);
     if (lane == 0 && t_issue < t_end) {
