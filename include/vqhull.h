@@ -174,7 +174,7 @@ typedef struct {
   double k2_ms;              /* per-segment finalize                          */
   double k3_ms;              /* small-segment finisher                        */
   double k4_ms;              /* ordering                                      */
-  double other_ms;           /* scans, counter resets                         */
+  double other_ms;           /* scans, tile maps, counter resets              */
 } vq_profile;
 
 vq_status vq_profile_read(vq_profile* out, int32_t reset);

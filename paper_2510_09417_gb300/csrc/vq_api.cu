@@ -258,8 +258,8 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   VQ_CHECK(tm.begin(kKindK0));
   VQ_CHECK(launch_k0(w, c.sms * 8, st));
   VQ_CHECK(launch_k0_finalize(w, st));
-  VQ_CHECK(launch_tilemap(w, 0, c.sms * 4, st));
   VQ_CHECK(tm.end());
+  VQ_TIMED(tm, kKindOther, launch_tilemap(w, 0, c.sms * 4, st));
   // which partition kernel: FP32-only unless some set needs the FP64 tier
   VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   VQ_CHECK(cudaStreamSynchronize(st));
@@ -275,7 +275,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
     if (k1_grid > 0) VQ_TIMED(tm, kKindK1, launch_k1(w, level, cfg.ppt, (int)k1_grid, st));
     c.prof.k1_launches++;
     VQ_TIMED(tm, kKindK2, launch_k2(w, level, c.sms * 8, st));
-    VQ_TIMED(tm, kKindK2, launch_tilemap(w, (level + 1) & 1, c.sms * 4, st));
+    VQ_TIMED(tm, kKindOther, launch_tilemap(w, (level + 1) & 1, c.sms * 4, st));
     VQ_TIMED(tm, kKindK3, launch_k3(w, c.sms * 2, st));
     VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     VQ_CHECK(cudaStreamSynchronize(st));
@@ -306,6 +306,9 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
             "vqhull k1prof tiles=%llu wait=%llu classify=%llu farthest=%llu atomic=%llu store=%llu issue=%llu "
             "total=%llu far_bounds=%llu far_searches=%llu multi_lane=%llu cands=%llu\n",
             q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8], q[9], q[10], q[11]);
+    const unsigned long long* r = c.h_ctrl->k2prof;
+    fprintf(stderr, "vqhull k2prof segments=%llu overflow=%llu candidates=%llu scanned=%llu\n", r[0], r[1], r[2],
+            r[3]);
   }
 #endif
   if (c.h_ctrl->dbg_site)

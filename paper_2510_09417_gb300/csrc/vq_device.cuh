@@ -68,8 +68,10 @@ struct Ctrl {
   int fill_jobs[2];         // tile-map fill jobs per level parity
   int any_slow;             // some point set needs the FP64 tier (|coordinate| >= 2^40)
   int pad0;
+  long long k1_nw[2];       // warps of the last partition launch per level parity
   long long dbg_val;        // checked builds: the offending value
   unsigned long long k1prof[12];  // profiling builds: partition-kernel cycle and event counters
+  unsigned long long k2prof[4];   // profiling builds: finalize counters
 };
 
 // A live segment: points off .. off+len-1 of its source buffer, hull edge

@@ -204,9 +204,31 @@ __device__ __forceinline__ LexPt shfl_lex(const LexPt& p, int m) {
   return o;
 }
 
-// Lexicographic min and max (x, then y, then lowest index) of each tile, as
-// integer comparisons of the coordinates' ordered bit patterns; also flags
-// non-finite values and magnitudes >= 2^40 (outside the FP32 tier's range).
+// One point's contribution to the extreme pass: lexicographic min and max
+// (x, then y, then lowest index) as integer comparisons of the ordered bit
+// patterns (branch-free selects: the batched loads stay in flight); am
+// keeps the largest magnitude bit pattern seen, from which the flags are
+// derived once (k0_flags).
+__device__ __forceinline__ void k0_take(double vx, double vy, int i, LexPt& mn, LexPt& mx,
+                                        unsigned long long& am) {
+  const LexPt p{order_key(vx), order_key(vy), i};
+  if (lex_min_better(p, mn)) mn = p;
+  if (lex_max_better(p, mx)) mx = p;
+  const unsigned long long ax = (unsigned long long)__double_as_longlong(vx) & 0x7fffffffffffffffull;
+  const unsigned long long ay = (unsigned long long)__double_as_longlong(vy) & 0x7fffffffffffffffull;
+  am = am > ax ? am : ax;
+  am = am > ay ? am : ay;
+}
+// bit 0: a coordinate is non-finite; bit 1: some |coordinate| >= 2^40
+// (outside the FP32 tier's range)
+__device__ __forceinline__ int k0_flags(unsigned long long am) {
+  return (am >= 0x7ff0000000000000ull ? 1 : 0) | (am >= 0x4270000000000000ull ? 2 : 0);
+}
+
+// Lexicographic min and max (x, then y, then lowest index) of each tile and
+// its flags.  Tiles whose first point is 16-byte aligned in both arrays
+// (the usual case) are read as pairs with 16-byte loads, eight pairs per
+// array in flight per thread; others point by point.
 __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
   __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
   __shared__ int s_fl[kK0Threads / kWarp];
@@ -223,18 +245,39 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
     const int begin = S.off + j * kK0Tile;
     const int count = min(kK0Tile, S.len - j * kK0Tile);
     LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
-    int fl = 0;
+    unsigned long long am = 0;
+    const bool vec = ((reinterpret_cast<uintptr_t>(w.x + begin) | reinterpret_cast<uintptr_t>(w.y + begin)) & 15u) == 0;
+    if (vec) {
+      // pair q covers points 2q, 2q+1; thread tid takes pairs tid + 256 k
+      const double2* px = reinterpret_cast<const double2*>(w.x + begin);
+      const double2* py = reinterpret_cast<const double2*>(w.y + begin);
+      const int npairs = count >> 1;
+      constexpr int B = 8;
+      for (int q0 = threadIdx.x; q0 < npairs; q0 += B * kK0Threads) {
+        double2 bx[B], by[B];
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+          const int q = q0 + k * kK0Threads;
+          if (q < npairs) {
+            bx[k] = __ldcs(px + q);
+            by[k] = __ldcs(py + q);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+          const int q = q0 + k * kK0Threads;
+          if (q < npairs) {
+            k0_take(bx[k].x, by[k].x, begin + 2 * q, mn, mx, am);
+            k0_take(bx[k].y, by[k].y, begin + 2 * q + 1, mn, mx, am);
+          }
+        }
+      }
+      if ((count & 1) && threadIdx.x == 0) k0_take(w.x[begin + count - 1], w.y[begin + count - 1], begin + count - 1, mn, mx, am);
+    } else {
 #pragma unroll 8
-    for (int l = threadIdx.x; l < count; l += kK0Threads) {
-      const double vx = w.x[begin + l], vy = w.y[begin + l];
-      const LexPt p{order_key(vx), order_key(vy), begin + l};
-      if (lex_min_better(p, mn)) mn = p;
-      if (lex_max_better(p, mx)) mx = p;
-      const unsigned long long ax = (unsigned long long)__double_as_longlong(vx) & 0x7fffffffffffffffull;
-      const unsigned long long ay = (unsigned long long)__double_as_longlong(vy) & 0x7fffffffffffffffull;
-      const unsigned long long am = ax > ay ? ax : ay;
-      fl |= (am >= 0x7ff0000000000000ull ? 1 : 0) | (am >= 0x4270000000000000ull ? 2 : 0);
+      for (int l = threadIdx.x; l < count; l += kK0Threads) k0_take(w.x[begin + l], w.y[begin + l], begin + l, mn, mx, am);
     }
+    int fl = k0_flags(am);
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
       const LexPt a = shfl_lex(mn, m), b = shfl_lex(mx, m);
@@ -264,16 +307,21 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
 // One warp per point set: p, q, the set's flags; emit p; make the level-0
 // segment (a = p, b = p, r = q), whose children are p->q (upper, points left
 // of p->q) and q->p (lower), the two calls of Alg. 1's first line.
-__global__ void k_k0_finalize(Work w) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int s = gw; s < w.nsets; s += nw) {
+__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl, int lane);
+
+// One block per point set: the set's tile partials are reduced by the whole
+// block, then warp 0 finishes the set.
+__global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
+  __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
+  __shared__ int s_fl[kK0Threads / kWarp];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int s = blockIdx.x; s < w.nsets; s += gridDim.x) {
     SetRec S = w.sets[s];
-    if (S.len == 0) continue;
+    if (S.len == 0) continue;  // uniform across the block
     LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
     int fl = 0;
-    for (int t = w.k0_tile_start[s] + lane; t < w.k0_tile_start[s + 1]; t += kWarp) {
+#pragma unroll 4
+    for (int t = w.k0_tile_start[s] + threadIdx.x; t < w.k0_tile_start[s + 1]; t += kK0Threads) {
       const K0Part P = w.k0part[t];
       const LexPt a{P.minx, P.miny, P.mini}, b{P.maxx, P.maxy, P.maxi};
       if (lex_min_better(a, mn)) mn = a;
@@ -287,12 +335,35 @@ __global__ void k_k0_finalize(Work w) {
       if (lex_max_better(b, mx)) mx = b;
       fl |= __shfl_xor_sync(kFull, fl, m);
     }
+    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; }
+    __syncthreads();
+    if (warp == 0) {
+      mn = lane < kK0Threads / kWarp ? s_mn[lane] : LexPt{LLONG_MAX, LLONG_MAX, INT_MAX};
+      mx = lane < kK0Threads / kWarp ? s_mx[lane] : LexPt{LLONG_MIN, LLONG_MIN, INT_MAX};
+      fl = lane < kK0Threads / kWarp ? s_fl[lane] : 0;
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) {
+        const LexPt a = shfl_lex(mn, m), b = shfl_lex(mx, m);
+        if (lex_min_better(a, mn)) mn = a;
+        if (lex_max_better(b, mx)) mx = b;
+        fl |= __shfl_xor_sync(kFull, fl, m);
+      }
+      k0_finish_set(w, s, S, mn, mx, fl, lane);
+    }
+    __syncthreads();  // the shared partials are reused by the next set
+  }
+}
+
+// Warp 0 of the finalize block: p, q and the flags of set s; emit p; make
+// the level-0 segment.
+__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl, int lane) {
+  {
     if (fl & 1) {
       if (lane == 0) {
         atomicOr(&w.ctrl->err, kErrNonfinite);
         atomicMin(reinterpret_cast<unsigned long long*>(&w.ctrl->nonfinite_set), (unsigned long long)s);
       }
-      continue;
+      return;
     }
     const int p = mn.i, q = mx.i;
     S.p = p;
@@ -303,7 +374,7 @@ __global__ void k_k0_finalize(Work w) {
       w.sets[s] = S;
       emit(w, (long long)S.off + S.shift, p - S.off);
     }
-    if (p == q) continue;  // all points coincide with p
+    if (p == q) return;  // all points coincide with p
     SegRec R;
     R.shift = S.shift;
     R.off = S.off;
@@ -780,6 +851,14 @@ __device__ BestRec seg_best(const Work& w, int par, int s, const SegRec& S, int 
   const int nc = __ldcg(&st->ncand[ch]);
   const double thr = dkey_inv(__ldcg(&st->lomax[ch]));
   CandT<double> best = cand_none<double>();
+#ifdef VQ_K1_PROFILE
+  if (lane == 0) {
+    atomicAdd(&w.ctrl->k2prof[0], 1ull);
+    if (nc > kMaxCand) atomicAdd(&w.ctrl->k2prof[1], 1ull);
+    atomicAdd(&w.ctrl->k2prof[2], (unsigned long long)(nc < kMaxCand ? nc : kMaxCand));
+    if (nc > kMaxCand) atomicAdd(&w.ctrl->k2prof[3], (unsigned long long)S.ntiles);
+  }
+#endif
   if (nc <= kMaxCand) {
     for (int i = lane; i < nc; i += kWarp) {
       const int t = __ldcg(&st->cand[ch][i]);
@@ -787,6 +866,28 @@ __device__ BestRec seg_best(const Work& w, int par, int s, const SegRec& S, int 
       if (r.idx < 0 || r.hi < thr) continue;
       const CandT<double> c = from_rec(r);
       if (cand_beats(L, c, best)) best = c;
+    }
+  } else if (!w.ordered) {
+    // The streaming partition kernel gave warp g of nw the tile range
+    // [T g / nw, T (g+1) / nw) and wrote records only at the last tile of
+    // each run of one segment: visit exactly those tiles of this segment.
+    const long long T = min(__ldcg(&w.ctrl->k1_tiles[par]), w.capT), nw = __ldcg(&w.ctrl->k1_nw[par]);
+    const long long tb = S.tile_base, te = tb + S.ntiles;
+    if (nw > 0 && T > 0 && te <= T) {
+      // the warp holding tile u is the last g with T g / nw <= u, i.e.
+      // g = ceil((u + 1) nw / T) - 1
+      long long g0 = ((tb + 1) * nw + T - 1) / T - 1, g1 = (te * nw + T - 1) / T - 1;
+      if (g0 > nw - 1) g0 = nw - 1;
+      if (g1 > nw - 1) g1 = nw - 1;
+      for (long long g = g0 + lane; g <= g1; g += kWarp) {
+        const long long b = T * g / nw, e = T * (g + 1) / nw;
+        const long long last = (e < te ? e : te) - 1;
+        if (last < (b > tb ? b : tb)) continue;  // no tile of this segment in the range
+        const BestRec r = load_rec(&w.cand[par][last].own[ch]);
+        if (r.idx < 0 || r.hi < thr) continue;
+        const CandT<double> c = from_rec(r);
+        if (cand_beats(L, c, best)) best = c;
+      }
     }
   } else {
     for (int t = S.tile_base + lane; t < S.tile_base + S.ntiles; t += kWarp) {
@@ -871,17 +972,19 @@ __global__ void k_k2(Work w, int level) {
 // ---------------------------------------------------------------------------
 
 struct Frame {
+  double ax, ay, bx, by;  // endpoint coordinates (no global reload per frame)
   int lo, hi;   // range in the warp's permutation buffer
   int a, b, r;  // global indices; r < 0 until computed
   int buf;
   int depth;
+  int pad;
 };
 
 // Exact farthest point of P[lo, hi) from the line E = {ox, oy, ex, ey}
 // (E in shared memory, read only by the exact tiers and the FP64 keys).
 template <bool FAST>
-__device__ int small_argmax(const double* X, const double* Y, const int* I, const unsigned short* P, int lo,
-                            int hi, const double* E, int lane) {
+__device__ CandT<double> small_argmax(const double* X, const double* Y, const int* I, const unsigned short* P,
+                                      int lo, int hi, const double* E, int lane) {
   typedef typename KeyOf<FAST>::T K;
   LineF L;
   if (FAST) L = make_line(E[0], E[1], E[2], E[3]);
@@ -893,7 +996,7 @@ __device__ int small_argmax(const double* X, const double* Y, const int* I, cons
     take_best(best, E, X[u], Y[u], I[u], key, err);
   }
   best = warp_best(E, best);
-  return best.idx;
+  return to_double(best);
 }
 
 // One warp finishes a segment of <= kK3Cap points held in shared memory:
@@ -905,7 +1008,8 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
   int top = 0;
   if (lane == 0) {
     Frame f;
-    f.lo = 0; f.hi = S.len; f.a = S.a; f.b = S.b; f.r = S.r; f.buf = 0; f.depth = 0;
+    f.ax = w.x[S.a]; f.ay = w.y[S.a]; f.bx = w.x[S.b]; f.by = w.y[S.b];
+    f.lo = 0; f.hi = S.len; f.a = S.a; f.b = S.b; f.r = S.r; f.buf = 0; f.depth = 0; f.pad = 0;
     stk[0] = f;
   }
   top = 1;
@@ -919,18 +1023,26 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
       return;
     unsigned short* Pin = f.buf ? P1 : P0;
     unsigned short* Pout = f.buf ? P0 : P1;
-    if (lane == 0) { E[0] = w.x[f.a]; E[1] = w.y[f.a]; E[2] = w.x[f.b]; E[3] = w.y[f.b]; }
+    if (lane == 0) { E[0] = f.ax; E[1] = f.ay; E[2] = f.bx; E[3] = f.by; }
     __syncwarp();
     int r = f.r;
-    if (r < 0)
-      r = fast ? small_argmax<true>(X, Y, I, Pin, f.lo, f.hi, E, lane)
-               : small_argmax<false>(X, Y, I, Pin, f.lo, f.hi, E, lane);
+    double rx = 0.0, ry = 0.0;
+    if (r < 0) {
+      const CandT<double> best = fast ? small_argmax<true>(X, Y, I, Pin, f.lo, f.hi, E, lane)
+                                      : small_argmax<false>(X, Y, I, Pin, f.lo, f.hi, E, lane);
+      r = best.idx;
+      rx = best.x;
+      ry = best.y;
+    } else if (lane == 0 && VQ_OK_IDX(w, 16, r, 0, w.N)) {
+      rx = w.x[r];
+      ry = w.y[r];
+    }
     if (r < 0) {
       if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
       return;
     }
     if (!VQ_OK_IDX(w, 16, r, 0, w.N)) return;
-    if (lane == 0) fill_geom(*G, E[0], E[1], E[2], E[3], w.x[r], w.y[r]);
+    if (lane == 0) fill_geom(*G, E[0], E[1], E[2], E[3], rx, ry);
     __syncwarp();
     LineF l1, l2;
     if (fast) { l1 = line1_of(*G); l2 = line2_of(*G); }
@@ -958,8 +1070,12 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
     }
     // children: left [lo, lo+nL) on a->r, right [hi-nR, hi) on r->b
     Frame cl, cr;
+    cl.ax = f.ax; cl.ay = f.ay; cl.bx = G->rx; cl.by = G->ry;
     cl.lo = f.lo; cl.hi = f.lo + nL; cl.a = f.a; cl.b = r; cl.r = -1; cl.buf = f.buf ^ 1; cl.depth = f.depth + 1;
+    cl.pad = 0;
+    cr.ax = G->rx; cr.ay = G->ry; cr.bx = f.bx; cr.by = f.by;
     cr.lo = f.hi - nR; cr.hi = f.hi; cr.a = r; cr.b = f.b; cr.r = -1; cr.buf = f.buf ^ 1; cr.depth = f.depth + 1;
+    cr.pad = 0;
     if (lane == 0) {
       if (nL == 1) { const int u = Pout[cl.lo]; emit(w, (long long)S.off + cl.lo + 1 + S.shift, I[u] - S.set_off); }
       if (nR == 1) { const int u = Pout[cr.lo]; emit(w, (long long)S.off + cr.lo + 1 + S.shift, I[u] - S.set_off); }
@@ -1227,11 +1343,10 @@ cudaError_t launch_k0(const Work& w, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st) {
-  const long long warps = w.nsets;
-  long long blocks = (warps * 32 + 255) / 256;
+  long long blocks = w.nsets;
   if (blocks > 4096) blocks = 4096;
   count_launch();
-  k_k0_finalize<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(w);
+  k_k0_finalize<<<(unsigned)(blocks > 0 ? blocks : 1), kK0Threads, 0, st>>>(w);
   return cudaGetLastError();
 }
 

@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Wor
   const long long gw = (long long)blockIdx.x * WPB + warp, nw = (long long)gridDim.x * WPB;
   const int t_begin = (int)((long long)ntiles * gw / nw), t_end = (int)((long long)ntiles * (gw + 1) / nw);
   const TileDesc* desc = w.tdesc[par];
+  if (gw == 0 && lane == 0) w.ctrl->k1_nw[par] = nw;  // the finalize kernel retraces the tile split
   if (lane == 0) {
     for (int s = 0; s < NS; s++) mbar_init(&R->full[s], 1);
     mbar_fence_init();
