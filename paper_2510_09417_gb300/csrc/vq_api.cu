@@ -59,6 +59,13 @@ struct Ctx {
   double* stage = nullptr;
   int* stage_out = nullptr;
   long long stage_n = 0;
+  // pipelined host path: copy stream, per-chunk events, merge buffers
+  cudaStream_t cstream = nullptr;
+  std::vector<cudaEvent_t> cev;
+  double* mxy = nullptr;  // 2 * mcap doubles: merge x then merge y
+  int* mid = nullptr;     // mcap original indices
+  int* mout = nullptr;    // mcap merge-hull indices
+  long long mcap = 0;
   // last call
   long long* d_stats = nullptr;
   int last_levels = 0;
@@ -221,10 +228,14 @@ static vq_status ctx_reserve(Ctx& c, size_t bytes) {
 }
 
 // The level loop shared by the single and batched entry points.
+// small_max_override > 0 replaces the small-segment threshold for this run
+// (hull-dense inputs finish faster level-synchronously than in the
+// shared-memory recursion, which walks one hull vertex per step).
 static vq_status run(Ctx& c, const double* x, const double* y, const long long* offsets, long long n_single,
                      int nsets, long long N, int* out, long long* hull_offsets, long long* h_out,
-                     cudaStream_t st) {
-  const Config cfg = get_cfg();
+                     cudaStream_t st, int small_max_override = 0) {
+  Config cfg = get_cfg();
+  if (small_max_override > 0) cfg.small_max = small_max_override;
   const long long nkeys = N + nsets;
   Work w;
   memset(&w, 0, sizeof w);
@@ -395,6 +406,134 @@ vq_status vq_hull2d_batched(const double* x, const double* y, const int64_t* off
              reinterpret_cast<long long*>(hull_offsets), nullptr, st);
 }
 
+// ---------------------------------------------------------------------------
+// Host entry point, pipelined.  The host-to-device link (about 211 GB/s on
+// GB300 machines here) moves the points slower than the hull is computed, so
+// for large pinned inputs the copy runs in chunks on a second stream while
+// each arrived chunk's hull is computed; the answer is then the hull of the
+// union of the chunk hulls' vertices (the strict hull of a union is the
+// strict hull of the parts' hulls).  The merge buffer lists the chunk hulls
+// in chunk order, so among coincident points the lowest merge index is the
+// lowest original index and the output is the same as the direct hull's.
+// When the chunk hulls grow large (most points on the hull), the call falls
+// back to one hull over the staged points.
+// ---------------------------------------------------------------------------
+
+constexpr long long kPipeMin = 1ll << 24;       // pipelined from this size
+constexpr long long kPipeMinChunk = 1ll << 23;  // chunks of at least this many points,
+constexpr int kPipeChunks = 4;                  // and at most this many chunks (each chunk hull has a fixed cost)
+constexpr int kMergeSmallMax = 32;              // small-segment threshold of the merge hull
+
+static bool host_pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// Returns VQ_OK with *done = false when the caller should run the plain
+// path on the (fully staged) points.
+static vq_status host_pipelined(Ctx& c, const double* xh, const double* yh, long long n, int32_t* out_h,
+                                long long* h, cudaStream_t st, bool* done) {
+  *done = false;
+  long long kPipeChunk = (n + kPipeChunks - 1) / kPipeChunks;
+  if (kPipeChunk < kPipeMinChunk) kPipeChunk = kPipeMinChunk;
+  kPipeChunk = (kPipeChunk + 255) & ~255ll;  // chunk starts stay 2 KB aligned
+  const long long nchunks = (n + kPipeChunk - 1) / kPipeChunk;
+  const long long mmax = n / 8;  // merge budget: beyond it the plain path is cheaper
+  if (!c.cstream) VQ_CHECK(cudaStreamCreateWithFlags(&c.cstream, cudaStreamNonBlocking));
+  while ((long long)c.cev.size() < nchunks + 1) {
+    cudaEvent_t e;
+    VQ_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c.cev.push_back(e);
+  }
+  if (c.mcap < mmax) {
+    if (c.mxy) cudaFree(c.mxy);
+    if (c.mid) cudaFree(c.mid);
+    if (c.mout) cudaFree(c.mout);
+    c.mxy = nullptr;
+    c.mid = nullptr;
+    c.mout = nullptr;
+    c.mcap = 0;
+    if (cudaMalloc(&c.mxy, sizeof(double) * 2 * mmax) != cudaSuccess ||
+        cudaMalloc(&c.mid, sizeof(int) * mmax) != cudaSuccess || cudaMalloc(&c.mout, sizeof(int) * mmax) != cudaSuccess) {
+      cudaGetLastError();
+      return VQ_ERR_NOMEM;
+    }
+    c.mcap = mmax;
+  }
+  // the workspace for a full-size run, reserved before any chunk runs (the
+  // fallback may need it; no allocation happens between chunks)
+  {
+    const Config cfg = get_cfg();
+    Work w;
+    memset(&w, 0, sizeof w);
+    const size_t total = layout(w, nullptr, n, 1, n + 1, cfg) + scan_bytes(n + 1, 1);
+    vq_status s = ctx_reserve(c, total);
+    if (s != VQ_OK) return s;
+  }
+  double* sx = c.stage;
+  double* sy = c.stage + n;
+  // copies: after any earlier work on `st`, all chunks back to back
+  VQ_CHECK(cudaEventRecord(c.cev[nchunks], st));
+  VQ_CHECK(cudaStreamWaitEvent(c.cstream, c.cev[nchunks], 0));
+  for (long long k = 0; k < nchunks; k++) {
+    const long long off = k * kPipeChunk, len = (n - off < kPipeChunk) ? n - off : kPipeChunk;
+    VQ_CHECK(cudaMemcpyAsync(sx + off, xh + off, sizeof(double) * len, cudaMemcpyHostToDevice, c.cstream));
+    VQ_CHECK(cudaMemcpyAsync(sy + off, yh + off, sizeof(double) * len, cudaMemcpyHostToDevice, c.cstream));
+    VQ_CHECK(cudaEventRecord(c.cev[k], c.cstream));
+  }
+  vq_status result = VQ_OK;
+  long long m = 0;
+  bool merge = true;
+  for (long long k = 0; k < nchunks; k++) {
+    const long long off = k * kPipeChunk, len = (n - off < kPipeChunk) ? n - off : kPipeChunk;
+    if (cudaStreamWaitEvent(st, c.cev[k], 0) != cudaSuccess) {
+      cudaGetLastError();
+      result = VQ_ERR_CUDA;
+      break;
+    }
+    long long hk = 0;
+    vq_status s = run(c, sx + off, sy + off, nullptr, len, 1, len, c.stage_out + off, nullptr, &hk, st);
+    if (s != VQ_OK) {
+      result = s;
+      merge = false;
+      break;
+    }
+    if (m + hk > mmax) {
+      merge = false;
+      break;
+    }
+    if (launch_gather(sx + off, sy + off, c.stage_out + off, hk, off, c.mxy + m, c.mxy + mmax + m, c.mid + m, st) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      result = VQ_ERR_CUDA;
+      break;
+    }
+    m += hk;
+  }
+  // the copies read the caller's buffers: they end before this call returns
+  VQ_CHECK(cudaStreamSynchronize(c.cstream));
+  if (result != VQ_OK) return result;
+  if (!merge) {
+    VQ_CHECK(cudaStreamWaitEvent(st, c.cev[nchunks - 1], 0));
+    return VQ_OK;  // *done stays false: plain path over the staged points
+  }
+  // the merge input is the chunk hulls' vertices: nearly every point is a
+  // hull vertex, so it runs level-synchronously to the end
+  long long hm = 0;
+  vq_status s = run(c, c.mxy, c.mxy + mmax, nullptr, m, 1, m, c.mout, nullptr, &hm, st, kMergeSmallMax);
+  if (s != VQ_OK) return s;
+  VQ_CHECK(launch_map_indices(c.mout, c.mid, hm, c.stage_out, st));
+  if (hm > 0) VQ_CHECK(cudaMemcpyAsync(out_h, c.stage_out, sizeof(int) * hm, cudaMemcpyDeviceToHost, st));
+  VQ_CHECK(cudaStreamSynchronize(st));
+  *h = hm;
+  *done = true;
+  return VQ_OK;
+}
+
 vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, int32_t* hull_idx_host,
                          int64_t* h, void* stream) {
   if (!h || n < 0) return VQ_ERR_INVALID_ARG;
@@ -424,8 +563,19 @@ vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, 
     }
     c->stage_n = n;
   }
-  VQ_CHECK(cudaMemcpyAsync(c->stage, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  VQ_CHECK(cudaMemcpyAsync(c->stage + n, y_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if (n >= kPipeMin && host_pinned(x_host) && host_pinned(y_host)) {
+    bool done = false;
+    long long hp = 0;
+    s = host_pipelined(*c, x_host, y_host, n, hull_idx_host, &hp, st, &done);
+    if (s != VQ_OK) return s;
+    if (done) {
+      *h = hp;
+      return VQ_OK;
+    }
+  } else {
+    VQ_CHECK(cudaMemcpyAsync(c->stage, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    VQ_CHECK(cudaMemcpyAsync(c->stage + n, y_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  }
   long long hh = 0;
   s = run(*c, c->stage, c->stage + n, nullptr, n, 1, n, c->stage_out, nullptr, &hh, st);
   if (s != VQ_OK && s != VQ_ERR_NONFINITE) return s;

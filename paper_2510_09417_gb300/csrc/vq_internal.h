@@ -66,6 +66,11 @@ cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st);
 cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long long* total,
                          long long* tmp, cudaStream_t st);
+// pipelined host path: chunk-hull points into the merge buffers, and merge
+// indices back to original indices
+cudaError_t launch_gather(const double* x, const double* y, const int* idx, long long m, long long base, double* mx,
+                          double* my, int* mid, cudaStream_t st);
+cudaError_t launch_map_indices(const int* mout, const int* mid, long long h, int* out, cudaStream_t st);
 cudaError_t scan_exclusive_i32(int* data, long long n, int* tmp, cudaStream_t st);
 cudaError_t scan_exclusive_i64(long long* data, long long n, long long* tmp, cudaStream_t st);
 long long scan_tmp_elems(long long n);

@@ -973,6 +973,7 @@ __global__ void k_k2(Work w, int level) {
 
 struct Frame {
   double ax, ay, bx, by;  // endpoint coordinates (no global reload per frame)
+  LineF la;               // FP32-tier constants of a->b (from the parent's geometry)
   int lo, hi;   // range in the warp's permutation buffer
   int a, b, r;  // global indices; r < 0 until computed
   int buf;
@@ -984,18 +985,28 @@ struct Frame {
 // (E in shared memory, read only by the exact tiers and the FP64 keys).
 template <bool FAST>
 __device__ CandT<double> small_argmax(const double* X, const double* Y, const int* I, const unsigned short* P,
-                                      int lo, int hi, const double* E, int lane) {
+                                      int lo, int hi, const double* E, const LineF& L, int lane) {
+  // the largest lower bound first (independent iterations), then exact
+  // comparisons only among the points whose upper bound reaches it
   typedef typename KeyOf<FAST>::T K;
-  LineF L;
-  if (FAST) L = make_line(E[0], E[1], E[2], E[3]);
+  K lmax = key_neg_inf<K>();
+  for (int l = lo + lane; l < hi; l += kWarp) {
+    const int u = P[l];
+    K key, err;
+    line_key_k(L, E, X[u], Y[u], key, err);
+    lmax = key_max(lmax, key_lo(key, err));
+  }
+  const K Lw = warp_max_k(lmax);
   CandT<K> best = cand_none<K>();
   for (int l = lo + lane; l < hi; l += kWarp) {
     const int u = P[l];
     K key, err;
     line_key_k(L, E, X[u], Y[u], key, err);
-    take_best(best, E, X[u], Y[u], I[u], key, err);
+    if (key_hi(key, err) >= Lw) take_best(best, E, X[u], Y[u], I[u], key, err);
   }
-  best = warp_best(E, best);
+  const unsigned lanes = __ballot_sync(kFull, best.idx >= 0);
+  if (__popc(lanes) > 1) best = warp_best(E, best);
+  else if (lanes) best = shfl_xor_cand(best, lane ^ (__ffs(lanes) - 1));
   return to_double(best);
 }
 
@@ -1009,6 +1020,7 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
   if (lane == 0) {
     Frame f;
     f.ax = w.x[S.a]; f.ay = w.y[S.a]; f.bx = w.x[S.b]; f.by = w.y[S.b];
+    f.la = fast ? make_line(f.ax, f.ay, f.bx, f.by) : LineF{};
     f.lo = 0; f.hi = S.len; f.a = S.a; f.b = S.b; f.r = S.r; f.buf = 0; f.depth = 0; f.pad = 0;
     stk[0] = f;
   }
@@ -1028,8 +1040,8 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
     int r = f.r;
     double rx = 0.0, ry = 0.0;
     if (r < 0) {
-      const CandT<double> best = fast ? small_argmax<true>(X, Y, I, Pin, f.lo, f.hi, E, lane)
-                                      : small_argmax<false>(X, Y, I, Pin, f.lo, f.hi, E, lane);
+      const CandT<double> best = fast ? small_argmax<true>(X, Y, I, Pin, f.lo, f.hi, E, f.la, lane)
+                                      : small_argmax<false>(X, Y, I, Pin, f.lo, f.hi, E, f.la, lane);
       r = best.idx;
       rx = best.x;
       ry = best.y;
@@ -1044,7 +1056,7 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
     if (!VQ_OK_IDX(w, 16, r, 0, w.N)) return;
     if (lane == 0) fill_geom(*G, E[0], E[1], E[2], E[3], rx, ry);
     __syncwarp();
-    LineF l1, l2;
+    LineF l1 = {}, l2 = {};
     if (fast) { l1 = line1_of(*G); l2 = line2_of(*G); }
     int nL = 0, nR = 0;
     for (int base = f.lo; base < f.hi; base += kWarp) {
@@ -1071,9 +1083,11 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
     // children: left [lo, lo+nL) on a->r, right [hi-nR, hi) on r->b
     Frame cl, cr;
     cl.ax = f.ax; cl.ay = f.ay; cl.bx = G->rx; cl.by = G->ry;
+    cl.la = l1;
     cl.lo = f.lo; cl.hi = f.lo + nL; cl.a = f.a; cl.b = r; cl.r = -1; cl.buf = f.buf ^ 1; cl.depth = f.depth + 1;
     cl.pad = 0;
     cr.ax = G->rx; cr.ay = G->ry; cr.bx = f.bx; cr.by = f.by;
+    cr.la = l2;
     cr.lo = f.hi - nR; cr.hi = f.hi; cr.a = r; cr.b = f.b; cr.r = -1; cr.buf = f.buf ^ 1; cr.depth = f.depth + 1;
     cr.pad = 0;
     if (lane == 0) {
@@ -1502,6 +1516,42 @@ int k1_blocks_per_sm(int ppt) {
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st) {
   count_launch();
   k_k2<<<grid, 256, 0, st>>>(w, level);
+  return cudaGetLastError();
+}
+
+// Chunk hull -> merge buffer: point idx[i] (chunk-local) of the chunk's
+// arrays, with its original index base + idx[i].
+__global__ void k_gather(const double* x, const double* y, const int* idx, long long m, long long base, double* mx,
+                         double* my, int* mid) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const int u = idx[i];
+    mx[i] = x[u];
+    my[i] = y[u];
+    mid[i] = (int)(base + u);
+  }
+}
+
+__global__ void k_map_indices(const int* mout, const int* mid, long long h, int* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < h; i += (long long)gridDim.x * blockDim.x)
+    out[i] = mid[mout[i]];
+}
+
+cudaError_t launch_gather(const double* x, const double* y, const int* idx, long long m, long long base, double* mx,
+                          double* my, int* mid, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  long long blocks = (m + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launch();
+  k_gather<<<(unsigned)blocks, 256, 0, st>>>(x, y, idx, m, base, mx, my, mid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_map_indices(const int* mout, const int* mid, long long h, int* out, cudaStream_t st) {
+  if (h <= 0) return cudaSuccess;
+  long long blocks = (h + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launch();
+  k_map_indices<<<(unsigned)blocks, 256, 0, st>>>(mout, mid, h, out);
   return cudaGetLastError();
 }
 

@@ -187,3 +187,29 @@ def test_all_points_on_hull(vq, ppt):
     for n, seed in ((100_000, 1), (150_001, 2), (200_000, 3)):
         x, y = synth.points("circle", n, seed)
         check(vq, x, y, stats=True)
+
+
+def _pinned(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory().numpy()
+
+
+@pytest.mark.parametrize("case", ["disk", "duplicates", "circle"])
+def test_host_entry_pipelined(vq, case):
+    """Pinned host inputs of >= 2^24 points take the chunked path (copies
+    overlapped with chunk hulls, then the hull of the chunk hulls): same
+    answer as the oracle, including the lowest index among coincident points
+    in different chunks and the fallback when chunk hulls are large."""
+    n = (1 << 24) + 12345
+    if case == "disk":
+        x, y = synth.points("disk", n, 21)
+    elif case == "duplicates":
+        a, b = synth.points("square", n // 2 + 1, 22)
+        x, y = np.concatenate([a, a])[:n], np.concatenate([b, b])[:n]
+    else:
+        x, y = synth.points("circle", n, 23)
+    got = vq.vq_hull2d_host(_pinned(x), _pinned(y))
+    if case == "circle":
+        code, bad = oracle.verify(x, y, got)
+        assert code == 0, (oracle.VERIFY_CODES.get(code), bad)
+    else:
+        assert np.array_equal(got, oracle.hull(x, y))
