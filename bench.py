@@ -41,9 +41,11 @@ METRIC = "Gpoints/s & % HBM peak per hull; batched hulls/s, p50/p99 vs plain (bi
 UNIT = "Gpoints/s"
 WORKLOAD = "single hulls: uniform square + uniform disk, 1e8 FP64 SoA points each (seeds 1, 2)"
 FULL_N = 100_000_000
-# DRAM traffic per partition launch from the committed ncu summary of the
-# current kernel (profiles/); None until a capture of this kernel exists.
-K1_TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes the partition kernel moves per algorithmic unit (point
+# classified or kept), from one ncu capture of all partition launches of a
+# 2e7-point disk hull (summarised under profiles/); traffic grows in
+# proportion to the units, so a launch's traffic is this times its units.
+K1_DRAM_BYTES_PER_UNIT = 17.59
 
 
 def parse():
@@ -252,10 +254,11 @@ def main():
     k1_bytes = 16.0 * (prof["k1_points_read"] + prof["k1_points_kept"])
     k1_s = prof["k1_ms"] / 1e3
     achieved = k1_bytes / k1_s / 1e9 if k1_s > 0 else 0.0
-    traffic = K1_TRAFFIC_BYTES_PER_LAUNCH
+    units_per_launch = (prof["k1_points_read"] + prof["k1_points_kept"]) / max(prof["k1_launches"], 1)
+    traffic = K1_DRAM_BYTES_PER_UNIT * units_per_launch
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_k1 (fused classify + compact + argmax)",
+                "kernel": "k_k1w (streaming partition: classify + compact + farthest point)",
                 "bytes_per_launch": k1_bytes / max(prof["k1_launches"], 1),
                 "ms_per_launch": prof["k1_ms"] / max(prof["k1_launches"], 1)}
 
