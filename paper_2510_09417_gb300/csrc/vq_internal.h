@@ -14,6 +14,7 @@ constexpr int kK0Tile = 8192;       // points per extreme-pass tile
 constexpr int kK3Cap = 1024;        // points per warp in the small-segment kernel
 constexpr int kK3Warps = 4;
 constexpr int kK3Stack = 24;
+constexpr int kK3StatLevels = 64;  // levels whose counters the small-segment kernel sums per warp
 constexpr int kK4Words = 1024;      // bitmap words per ordering block (256 threads x 4)
 constexpr int kFillTiles = 1024;    // tiles per tile-map fill job
 

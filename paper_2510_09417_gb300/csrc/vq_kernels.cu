@@ -1013,7 +1013,8 @@ __device__ CandT<double> small_argmax(const double* X, const double* Y, const in
 // One warp finishes a segment of <= kK3Cap points held in shared memory:
 // Alg. 1's recursion with an explicit stack, one partition per step.
 __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y, int* I, unsigned short* P0,
-                            unsigned short* P1, Frame* stk, SegGeom* G, double* E, int lane) {
+                            unsigned short* P1, Frame* stk, SegGeom* G, double* E, unsigned long long* kst,
+                            int lane) {
   const bool fast = (S.flags & kSegFast) != 0;
   const unsigned lt = lanemask_lt();
   int top = 0;
@@ -1078,7 +1079,14 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
     __syncwarp();
     if (lane == 0) {
       emit(w, (long long)S.off + f.lo + nL + 1 + S.shift, r - S.set_off);
-      add_stats(w, S.level + f.depth, f.hi - f.lo, nL + nR);
+      const int lvl = S.level + f.depth;
+      if (lvl < kK3StatLevels) {
+        kst[lvl] += (unsigned long long)(f.hi - f.lo);
+        kst[kK3StatLevels + lvl] += (unsigned long long)(nL + nR);
+        kst[2 * kK3StatLevels + lvl] += 1ull;
+      } else {
+        add_stats(w, lvl, f.hi - f.lo, nL + nR);
+      }
     }
     // children: left [lo, lo+nL) on a->r, right [hi-nR, hi) on r->b
     Frame cl, cr;
@@ -1116,8 +1124,12 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
   }
 }
 
-static constexpr size_t kK3PerWarp =
-    (size_t)kK3Cap * 24 + sizeof(Frame) * kK3Stack + sizeof(SegGeom) + 4 * sizeof(double);
+// Per-level counters of the small-segment kernel are summed per warp in
+// shared memory (levels below kK3StatLevels) and added to the call's
+// counters once, when the warp finishes: one atomic per level and counter
+// instead of one per frame (hull-dense inputs have a frame per vertex).
+static constexpr size_t kK3PerWarp = (size_t)kK3Cap * 24 + sizeof(Frame) * kK3Stack + sizeof(SegGeom) +
+                                     4 * sizeof(double) + 3 * kK3StatLevels * sizeof(unsigned long long);
 
 __global__ void __launch_bounds__(kK3Warps * kWarp) k_k3(Work w) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1132,6 +1144,9 @@ __global__ void __launch_bounds__(kK3Warps * kWarp) k_k3(Work w) {
   SegGeom* G = reinterpret_cast<SegGeom*>(P1 + kK3Cap);  // 8-byte aligned: 24 * kK3Cap bytes precede it
   double* E = reinterpret_cast<double*>(G + 1);
   Frame* stk = reinterpret_cast<Frame*>(E + 4);
+  unsigned long long* kst = reinterpret_cast<unsigned long long*>(stk + kK3Stack);
+  for (int i = lane; i < 3 * kK3StatLevels; i += kWarp) kst[i] = 0ull;
+  __syncwarp();
   const int nq = min(*reinterpret_cast<volatile int*>(&w.ctrl->k3_count), w.capQ);
   for (int e = blockIdx.x * kK3Warps + warp; e < nq; e += gridDim.x * kK3Warps) {
     const SegRec S = w.k3q[e];
@@ -1150,6 +1165,7 @@ __global__ void __launch_bounds__(kK3Warps * kWarp) k_k3(Work w) {
       const int b = (S.flags & kSegSrcBuf1) ? 1 : 0;
       sx = w.bx[b]; sy = w.by[b]; si = w.bi[b];
     }
+#pragma unroll 4
     for (int l = lane; l < S.len; l += kWarp) {
       X[l] = sx[S.off + l];
       Y[l] = sy[S.off + l];
@@ -1157,8 +1173,15 @@ __global__ void __launch_bounds__(kK3Warps * kWarp) k_k3(Work w) {
       P0[l] = (unsigned short)l;
     }
     __syncwarp();
-    small_solve(w, S, X, Y, I, P0, P1, stk, G, E, lane);
+    small_solve(w, S, X, Y, I, P0, P1, stk, G, E, kst, lane);
     __syncwarp();
+  }
+  // this warp's per-level counters into the call's
+  for (int l = lane; l < kK3StatLevels; l += kWarp) {
+    if (kst[2 * kK3StatLevels + l] == 0ull) continue;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[l]), kst[l]);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[kMaxLevels + l]), kst[kK3StatLevels + l]);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[2 * kMaxLevels + l]), kst[2 * kK3StatLevels + l]);
   }
 }
 
