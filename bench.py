@@ -74,10 +74,8 @@ def peaks():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2510_09417_gb300.replicas import dist_env as env
+    return env()
 
 
 def cpu_oracle_rate(n_sample: int):
@@ -242,12 +240,10 @@ def main():
     ms = ev0.elapsed_time(ev1)
     prof = vq.vq_profile_read(reset=True)
     vq.vq_set_config(profile=0)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    from paper_2510_09417_gb300.replicas import job_rate, max_over_ranks
+    ms_max = max_over_ranks(ms, device="cuda")
     pts_step = 2 * n * ws
-    value = pts_step * args.steps / (ms_max / 1e3) / 1e9
+    value = job_rate(2 * n * args.steps, ws, ms_max / 1e3) / 1e9
 
     # roofline of the partition kernel: paper-model bytes / event time
     peak, peak_kind = peaks()
@@ -281,10 +277,7 @@ def main():
             hs = e2e_step()
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
-        sec_t = torch.tensor([sec], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(sec_t, op=dist.ReduceOp.MAX)
-        sec = float(sec_t.item())
+        sec = max_over_ranks(sec, device="cuda")
         e2e = {"value": pts_step * ksteps / sec / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 2 * 16 * n, "d2h_bytes_per_step": 4 * int(sum(hs)),
                "steps": ksteps, "api": "vq_hull2d_host (pinned host buffers)"}
