@@ -99,19 +99,13 @@ struct alignas(16) K1Stage {
 };
 static_assert(sizeof(SegGeom) == 96, "SegGeom is bulk-copied as 96 bytes");
 
-// A warp's private region: its stages, the upper bounds of its points'
-// keys (FP32; FP64 bounds are rounded up, which only widens the candidate
-// filter) and the stages' mbarriers.
+// A warp's private region: its stages and their mbarriers.
 template <int PPT, int NS>
 struct alignas(16) K1Ring {
   static constexpr int TW = 32 * PPT;
   K1Stage<TW> st[NS];
-  float hs[TW];
   unsigned long long full[NS];
 };
-
-__device__ __forceinline__ float hs_up(float v) { return v; }
-__device__ __forceinline__ float hs_up(double v) { return __double2float_ru(v); }
 
 // Pass-A classification.  FP32 tier: both lines are evaluated without
 // branches; 1 / 2 = left / right child, 0 = discard, 3 = undecided (the
@@ -305,9 +299,8 @@ __device__ __forceinline__ void k1w_flush(const Work& w, int par, K1Run& r, int 
 // ---- one warp tile ----
 
 template <int PPT, bool SRC_INPUT, bool FAST>
-__device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PPT>* __restrict__ sg,
-                                         float* __restrict__ hs, int lane, K1Run& run,
-                                         unsigned long long* prof) {
+__device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PPT>* __restrict__ sg, int lane,
+                                         K1Run& run, unsigned long long* prof) {
   (void)prof;
   K1_MARK(c0);
   typedef typename KeyOf<FAST>::T K;
@@ -333,8 +326,8 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
     w.cand[par][t].own[1].idx = -1;
   }
 
-  // pass A: filter tier for every point; upper bounds of survivors' keys
-  // go to hs[k * 32 + lane], undecided points are flagged
+  // pass A: filter tier for every point; class masks, undecided points
+  // flagged, per-lane maxima of the keys' bounds per child
   unsigned m1 = 0, m2 = 0, und = 0;
   K lo0 = key_neg_inf<K>(), lo1 = key_neg_inf<K>(), hi0 = key_neg_inf<K>(), hi1 = key_neg_inf<K>();
   LineF l1 = {}, l2 = {};
@@ -345,16 +338,14 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
 #pragma unroll
   for (int k = 0; k < PPT; k++) {
     const int l = k * kWarp + lane;
-    K h = key_neg_inf<K>();
     if (l < count) {
       K key, err;
       const int c = classify_a(*G, l1, l2, X[l], Y[l], key, err);
       const K lo = key_lo(key, err), hi = key_hi(key, err);
       if (c == 3) und |= 1u << k;
-      if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); h = hi; }
-      if (c == 2) { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); h = hi; }
+      if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); }
+      if (c == 2) { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); }
     }
-    hs[l] = hs_up(h);
   }
   // exact tiers for the undecided points (rare)
   if (__any_sync(kFull, und != 0)) {
@@ -370,7 +361,6 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
         const K lo = key_lo(key, err), hi = key_hi(key, err);
         if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); }
         else { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); }
-        hs[l] = hs_up(hi);
       }
     }
   }
@@ -403,11 +393,16 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
     const K Lc = ch ? L1 : L0;
     const K thr = have && rlo > Lc ? rlo : Lc;
     const unsigned mc = ch ? m2 : m1;
-    unsigned cm = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; k++)
-      if (((mc >> k) & 1u) && (K)hs[k * kWarp + lane] >= thr) cm |= 1u << k;
     const double* E = ch ? &G->rx : &G->ax;
+    // the survivors' keys again (the same evaluation as in pass A, so the
+    // same values): candidates reach the threshold
+    unsigned cm = 0;
+    for (unsigned u = mc; u != 0; u &= u - 1) {
+      const int l = (__ffs(u) - 1) * kWarp + lane;
+      K key, err;
+      line_key_k(ch ? l2 : l1, E, X[l], Y[l], key, err);
+      if (key_hi(key, err) >= thr) cm |= 1u << (__ffs(u) - 1);
+    }
     const unsigned lanes = __ballot_sync(kFull, cm != 0);
     if (lanes == 0) continue;
     K1_ADD(prof, 11, (unsigned long long)__reduce_add_sync(kFull, __popc(cm)));
@@ -481,10 +476,10 @@ struct K1W {
   static constexpr int TW = 32 * PPT;
   static constexpr size_t smem = (size_t)WPB * sizeof(Ring);
   // blocks per SM that shared memory allows (227 KB usable, 1 KB reserved
-  // per block), but never so many that a thread gets fewer than 96
+  // per block), but never so many that a thread gets fewer than 112
   // registers: the register budget is sized for MINB blocks
   static constexpr int SMEMB = (int)((227u * 1024u) / (smem + 1024u));
-  static constexpr int REGB = 65536 / (32 * WPB * 96);
+  static constexpr int REGB = 65536 / (32 * WPB * 112);
   static constexpr int MINB = SMEMB < REGB ? (SMEMB > 0 ? SMEMB : 1) : REGB;
 };
 
@@ -550,9 +545,9 @@ __global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Wor
     }
     K1Stage<32 * PPT>* sg = &R->st[s];
     if (ALLFAST || (sg->m.flags & kSegFast))
-      k1w_tile<PPT, SRC_INPUT, true>(w, par, sg, R->hs, lane, run, prof);
+      k1w_tile<PPT, SRC_INPUT, true>(w, par, sg, lane, run, prof);
     else
-      k1w_tile<PPT, SRC_INPUT, ALLFAST>(w, par, sg, R->hs, lane, run, prof);
+      k1w_tile<PPT, SRC_INPUT, ALLFAST>(w, par, sg, lane, run, prof);
     __syncwarp();
     K1_MARK(i0);
     if (lane == 0 && t_issue < t_end) {
