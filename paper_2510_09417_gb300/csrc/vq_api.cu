@@ -320,6 +320,10 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
     const unsigned long long* r = c.h_ctrl->k2prof;
     fprintf(stderr, "vqhull k2prof segments=%llu overflow=%llu candidates=%llu scanned=%llu\n", r[0], r[1], r[2],
             r[3]);
+    const unsigned long long* k = c.h_ctrl->k3prof;
+    fprintf(stderr,
+            "vqhull k3prof frames=%llu argmax=%llu geom=%llu classify=%llu points=%llu exact=%llu frame_total=%llu\n",
+            k[0], k[1], k[2], k[3], k[4], k[5], k[6]);
   }
 #endif
   if (c.h_ctrl->dbg_site)

@@ -72,6 +72,7 @@ struct Ctrl {
   long long dbg_val;        // checked builds: the offending value
   unsigned long long k1prof[12];  // profiling builds: partition-kernel cycle and event counters
   unsigned long long k2prof[4];   // profiling builds: finalize counters
+  unsigned long long k3prof[8];   // profiling builds: small-segment kernel counters
 };
 
 // A live segment: points off .. off+len-1 of its source buffer, hull edge
@@ -400,6 +401,7 @@ struct CandT {
 
 static __device__ __forceinline__ bool beats_exact(double ox, double oy, double ex, double ey, double ux, double uy, int ui,
                                          double vx, double vy, int vi) {
+  if (ux == vx && uy == vy) return ui < vi;  // coincident: cross and dot are exactly 0
   double det, bound;
   bool sure;
   int c = cross_f64(ox, oy, ex, ey, vx, vy, ux, uy, det, bound, sure);
@@ -589,8 +591,12 @@ __device__ __forceinline__ int classify_filter(const SegGeom& g, const LineF&, c
   return s2 > 0 ? 2 : 0;
 }
 
-// Exact classification (tiers 2 and 3).
+// Exact classification (tiers 2 and 3).  A point coincident with r (r
+// itself is in its segment's set) has orient exactly 0 against both lines:
+// it is discarded without the expansions, which the FP64 filter cannot
+// avoid for an exact zero (about 33K cycles per call on GB300).
 __device__ __forceinline__ int classify_exact(const SegGeom* g, double ux, double uy) {
+  if (ux == g->rx && uy == g->ry) return 0;
   if (orient_sign_slow(g->ax, g->ay, g->rx, g->ry, ux, uy) > 0) return 1;
   if (orient_sign_slow(g->rx, g->ry, g->bx, g->by, ux, uy) > 0) return 2;
   return 0;

@@ -1027,7 +1027,16 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
   }
   top = 1;
   __syncwarp();
+#ifdef VQ_K1_PROFILE
+  // [0] frames, [1] argmax cycles, [2] geometry cycles, [3] classify cycles,
+  // [4] points classified, [5] points sent to the exact tiers, [6] frame total
+  unsigned long long kp[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+#define K3_MARK(v) const unsigned long long v = clock64()
+#else
+#define K3_MARK(v)
+#endif
   while (top > 0) {
+    K3_MARK(q0);
     top--;
     const Frame f = stk[top];
     __syncwarp();
@@ -1050,6 +1059,7 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
       rx = w.x[r];
       ry = w.y[r];
     }
+    K3_MARK(q1);
     if (r < 0) {
       if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
       return;
@@ -1057,6 +1067,7 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
     if (!VQ_OK_IDX(w, 16, r, 0, w.N)) return;
     if (lane == 0) fill_geom(*G, E[0], E[1], E[2], E[3], rx, ry);
     __syncwarp();
+    K3_MARK(q2);
     LineF l1 = {}, l2 = {};
     if (fast) { l1 = line1_of(*G); l2 = line2_of(*G); }
     int nL = 0, nR = 0;
@@ -1068,6 +1079,10 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
         u = Pin[l];
         if (fast) { float k, e; c = classify_filter(*G, l1, l2, X[u], Y[u], k, e); }
         else { double k, e; c = classify_filter(*G, l1, l2, X[u], Y[u], k, e); }
+#ifdef VQ_K1_PROFILE
+        kp[4]++;
+        if (c == 3) kp[5]++;
+#endif
         if (c == 3) c = classify_exact(G, X[u], Y[u]);
       }
       const unsigned mL = __ballot_sync(kFull, c == 1), mR = __ballot_sync(kFull, c == 2);
@@ -1077,6 +1092,13 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
       nR += __popc(mR);
     }
     __syncwarp();
+    K3_MARK(q3);
+#ifdef VQ_K1_PROFILE
+    kp[0]++;
+    kp[1] += q1 - q0;
+    kp[2] += q2 - q1;
+    kp[3] += q3 - q2;
+#endif
     if (lane == 0) {
       emit(w, (long long)S.off + f.lo + nL + 1 + S.shift, r - S.set_off);
       const int lvl = S.level + f.depth;
@@ -1121,7 +1143,18 @@ __device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y
     }
     top += need;
     __syncwarp();
+#ifdef VQ_K1_PROFILE
+    K3_MARK(q4);
+    kp[6] += q4 - q0;
+#endif
   }
+#ifdef VQ_K1_PROFILE
+  kp[4] = __reduce_add_sync(kFull, (unsigned)kp[4]);  // per-lane point counts: warp totals
+  kp[5] = __reduce_add_sync(kFull, (unsigned)kp[5]);
+  if (lane == 0)
+    for (int i = 0; i < 7; i++) atomicAdd(&w.ctrl->k3prof[i], kp[i]);
+#endif
+#undef K3_MARK
 }
 
 // Per-level counters of the small-segment kernel are summed per warp in
