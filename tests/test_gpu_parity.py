@@ -213,3 +213,27 @@ def test_host_entry_pipelined(vq, case):
         assert code == 0, (oracle.VERIFY_CODES.get(code), bad)
     else:
         assert np.array_equal(got, oracle.hull(x, y))
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+def test_extreme_ties_within_pairs(vq, shift):
+    """The lexicographic extremes repeated at both points of a 16-byte pair
+    of the extreme pass (and at odd offsets): the lowest index represents
+    them, at the start and at the turn of the hull."""
+    rng = np.random.default_rng(31 + shift)
+    n = 50_000
+    x, y = rng.random(n) + 1.0, rng.random(n) + 1.0
+    for base in (2 + shift, 1000 + shift, 4096 + shift):
+        x[base:base + 2] = 0.5       # lex-min, twice in a row
+        y[base:base + 2] = 1.5
+    for base in (6 + shift, 2000 + shift, 8190 + shift):
+        x[base:base + 2] = 2.5       # lex-max, twice in a row
+        y[base:base + 2] = 1.25
+    check(vq, x, y)
+    # the same through a batched call whose sets start at odd offsets
+    offs = np.array([0, 1, 333, n], dtype=np.int64)
+    hi, ho = vq.vq_hull2d_batched(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(offs).cuda())
+    hi, ho = hi.cpu().numpy(), ho.cpu().numpy()
+    for s in range(3):
+        a, b = offs[s], offs[s + 1]
+        assert np.array_equal(hi[ho[s]:ho[s + 1]], oracle.hull(x[a:b], y[a:b])), s
