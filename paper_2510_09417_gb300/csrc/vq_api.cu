@@ -426,6 +426,10 @@ vq_status vq_hull2d_batched(const double* x, const double* y, const int64_t* off
 constexpr long long kPipeMin = 1ll << 24;       // pipelined from this size
 constexpr long long kPipeMinChunk = 1ll << 23;  // chunks of at least this many points,
 constexpr int kPipeChunks = 4;                  // and at most this many chunks (each chunk hull has a fixed cost)
+// Chunk sizes as fractions of n: the last chunk is the smallest, so little
+// hull work is left when the last copy lands; every other chunk's hull
+// still finishes before the next chunk has arrived.
+constexpr double kPipeFrac[kPipeChunks] = {0.30, 0.30, 0.25, 0.15};
 constexpr int kMergeSmallMax = 32;              // small-segment threshold of the merge hull
 
 static bool host_pinned(const void* p) {
@@ -442,10 +446,28 @@ static bool host_pinned(const void* p) {
 static vq_status host_pipelined(Ctx& c, const double* xh, const double* yh, long long n, int32_t* out_h,
                                 long long* h, cudaStream_t st, bool* done) {
   *done = false;
-  long long kPipeChunk = (n + kPipeChunks - 1) / kPipeChunks;
-  if (kPipeChunk < kPipeMinChunk) kPipeChunk = kPipeMinChunk;
-  kPipeChunk = (kPipeChunk + 255) & ~255ll;  // chunk starts stay 2 KB aligned
-  const long long nchunks = (n + kPipeChunk - 1) / kPipeChunk;
+  // chunk k is [bnd[k], bnd[k+1]); starts stay 2 KB aligned
+  long long bnd[kPipeChunks + 1];
+  long long nchunks = 0;
+  bnd[0] = 0;
+  double acc = 0.0;
+  for (int k = 0; k < kPipeChunks; k++) {
+    acc += kPipeFrac[k];
+    long long e = k == kPipeChunks - 1 ? n : (((long long)(acc * (double)n)) + 255) & ~255ll;
+    if (e > n) e = n;
+    if (e - bnd[nchunks] < kPipeMinChunk && e < n) continue;  // too small: joins the next chunk
+    bnd[++nchunks] = e;
+    if (e == n) break;
+  }
+  if (nchunks > 1 && bnd[nchunks] - bnd[nchunks - 1] < kPipeMinChunk) {  // a short tail joins its predecessor
+    bnd[nchunks - 1] = n;
+    nchunks--;
+  }
+  if (nchunks < 2) {  // nothing to overlap: stage the points for the plain path
+    VQ_CHECK(cudaMemcpyAsync(c.stage, xh, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    VQ_CHECK(cudaMemcpyAsync(c.stage + n, yh, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    return VQ_OK;
+  }
   const long long mmax = n / 8;  // merge budget: beyond it the plain path is cheaper
   if (!c.cstream) VQ_CHECK(cudaStreamCreateWithFlags(&c.cstream, cudaStreamNonBlocking));
   while ((long long)c.cev.size() < nchunks + 1) {
@@ -484,7 +506,7 @@ static vq_status host_pipelined(Ctx& c, const double* xh, const double* yh, long
   VQ_CHECK(cudaEventRecord(c.cev[nchunks], st));
   VQ_CHECK(cudaStreamWaitEvent(c.cstream, c.cev[nchunks], 0));
   for (long long k = 0; k < nchunks; k++) {
-    const long long off = k * kPipeChunk, len = (n - off < kPipeChunk) ? n - off : kPipeChunk;
+    const long long off = bnd[k], len = bnd[k + 1] - bnd[k];
     VQ_CHECK(cudaMemcpyAsync(sx + off, xh + off, sizeof(double) * len, cudaMemcpyHostToDevice, c.cstream));
     VQ_CHECK(cudaMemcpyAsync(sy + off, yh + off, sizeof(double) * len, cudaMemcpyHostToDevice, c.cstream));
     VQ_CHECK(cudaEventRecord(c.cev[k], c.cstream));
@@ -493,7 +515,7 @@ static vq_status host_pipelined(Ctx& c, const double* xh, const double* yh, long
   long long m = 0;
   bool merge = true;
   for (long long k = 0; k < nchunks; k++) {
-    const long long off = k * kPipeChunk, len = (n - off < kPipeChunk) ? n - off : kPipeChunk;
+    const long long off = bnd[k], len = bnd[k + 1] - bnd[k];
     if (cudaStreamWaitEvent(st, c.cev[k], 0) != cudaSuccess) {
       cudaGetLastError();
       result = VQ_ERR_CUDA;

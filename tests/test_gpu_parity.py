@@ -195,11 +195,12 @@ def _pinned(a):
 
 @pytest.mark.parametrize("case", ["disk", "duplicates", "circle"])
 def test_host_entry_pipelined(vq, case):
-    """Pinned host inputs of >= 2^24 points take the chunked path (copies
-    overlapped with chunk hulls, then the hull of the chunk hulls): same
-    answer as the oracle, including the lowest index among coincident points
-    in different chunks and the fallback when chunk hulls are large."""
-    n = (1 << 24) + 12345
+    """Pinned host inputs large enough for several chunks (here three) take
+    the chunked path (copies overlapped with chunk hulls, then the hull of
+    the chunk hulls): same answer as the oracle, including the lowest index
+    among coincident points in different chunks and the fallback when chunk
+    hulls are large."""
+    n = (1 << 25) + 12345
     if case == "disk":
         x, y = synth.points("disk", n, 21)
     elif case == "duplicates":
