@@ -267,7 +267,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   VQ_CHECK(scan_exclusive_i32(w.k0_tile_start, (long long)nsets + 1, reinterpret_cast<int*>(scan_tmp), st));
   VQ_CHECK(tm.end());
   VQ_CHECK(tm.begin(kKindK0));
-  VQ_CHECK(launch_k0(w, c.sms * 8, st));
+  VQ_CHECK(launch_k0(w, c.sms * 2, st));  // resident blocks only (2 per SM); tiles of kK0Tile points
   VQ_CHECK(launch_k0_finalize(w, st));
   VQ_CHECK(tm.end());
   VQ_TIMED(tm, kKindOther, launch_tilemap(w, 0, c.sms * 4, st));

@@ -162,7 +162,7 @@ extern "C" vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t
   NA_CHECK(cudaMemsetAsync(w.bitmap, 0, sizeof(unsigned) * ((w.nkeys + 31) / 32 + 1), st));
   NA_CHECK(launch_seed(w, st));
   NA_CHECK(scan_exclusive_i32(w.k0_tile_start, 2, reinterpret_cast<int*>(scan_tmp), st));
-  NA_CHECK(launch_k0(w, d.sms * 8, st));
+  NA_CHECK(launch_k0(w, d.sms * 2, st));
   NA_CHECK(launch_k0_finalize(w, st));
   NA_CHECK(launch_tilemap(w, 0, d.sms * 4, st));
   NA_CHECK(cudaMemcpyAsync(&g_ctrl_host, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
