@@ -175,7 +175,12 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_points_per_hull": m},
+        "data": "synthetic",
+        # the same workload as the device arm; each step hulls a bounded
+        # sample of it (see cpu_baseline.sample)
+        "config": {"workload": WORKLOAD, "points_per_hull": args.n, "hulls_per_step": 2,
+                   "l2": "no flush: each input (1.6 GB at 1e8 points) exceeds L2",
+                   "parallelism": "replicas x1", "sample_points_per_hull": m},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
