@@ -9,6 +9,15 @@ larger than L2, so no flush is needed between steps.
 
 Reported (one JSON line on rank 0):
   value       Gpoints/s over the timed steps (device time, CUDA events);
+  batched     the 4096-set workload (sizes log-uniform in [64, 1e6], mixed
+              distributions) in one vq_hull2d_batched call vs 4096
+              sequential vq_hull2d calls on the same device-resident sets:
+              hulls/s of both, and whether every hull is identical;
+  serving     Poisson arrivals of requests (sizes log-uniform in [100, 1e7],
+              mixed distributions) through the continuous-batching server
+              (40 GB budget) vs one vq_hull2d_host call per request in
+              arrival order: p50/p99 latency from arrival and hulls/s at
+              rates up to past the plain path's saturation;
   e2e         the same through vq_hull2d_host from pinned host memory,
               host->device copy and result read-back inside the timing;
   roofline    the partition kernel (k_k1): paper-model bytes (16 per point
@@ -61,7 +70,158 @@ def parse():
                     help="points per workload for the CPU-oracle baseline")
     ap.add_argument("--ppt", type=int, default=0, help="tuning: points per lane of the partition kernel")
     ap.add_argument("--small-max", type=int, default=0, help="tuning: small-segment threshold")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=128)
     return ap.parse_args()
+
+
+WORKERS = max(1, min(16, os.cpu_count() or 1))
+
+
+def bench_batched(vq, torch, stream, steps):
+    """One vq_hull2d_batched call over the 4096-set workload against 4096
+    sequential vq_hull2d calls on the same device-resident sets."""
+    x, y, offs, dists = synth.batched_sets(workers=WORKERS)
+    nsets, total = len(offs) - 1, int(offs[-1])
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    od = torch.from_numpy(offs).cuda()
+    del x, y
+    hi = torch.empty(total, dtype=torch.int32, device="cuda")
+    ho = torch.empty(nsets + 1, dtype=torch.int64, device="cuda")
+    vq.vq_hull2d_batched(xd, yd, od, hi, ho, stream=stream)  # warm-up: workspace, graph
+    k = max(1, min(steps, 3))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        vq.vq_hull2d_batched(xd, yd, od, hi, ho, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batched = e0.elapsed_time(e1) / k
+    # sequential plain calls, one per set
+    out = torch.empty(int((offs[1:] - offs[:-1]).max()), dtype=torch.int32, device="cuda")
+    for s in range(min(nsets, 64)):
+        vq.vq_hull2d(xd[offs[s]:offs[s + 1]], yd[offs[s]:offs[s + 1]], out, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(nsets):
+        vq.vq_hull2d(xd[offs[s]:offs[s + 1]], yd[offs[s]:offs[s + 1]], out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    # every set's batched hull against its plain hull (untimed)
+    hof = ho.cpu().numpy()
+    mismatched = 0
+    neq = torch.zeros((), dtype=torch.int64, device="cuda")
+    for s in range(nsets):
+        h = vq.vq_hull2d(xd[offs[s]:offs[s + 1]], yd[offs[s]:offs[s + 1]], out, stream=stream)
+        if h.shape[0] != hof[s + 1] - hof[s]:
+            mismatched += 1
+        else:
+            neq += (hi[hof[s]:hof[s + 1]] != h).sum()
+    mismatched += int(neq.item() > 0)
+    del xd, yd, od, hi, ho, out
+    torch.cuda.empty_cache()
+    return {"workload": f"{nsets} sets, sizes log-uniform in [64, 1e6], distributions mixed (seed 5)",
+            "sets": nsets, "points": total,
+            "batched_ms": ms_batched, "batched_hulls_per_s": nsets / (ms_batched / 1e3),
+            "batched_gpoints_per_s": total / (ms_batched / 1e3) / 1e9,
+            "sequential_ms": ms_seq, "sequential_hulls_per_s": nsets / (ms_seq / 1e3),
+            "speedup": ms_seq / ms_batched, "identical_to_plain_calls": mismatched == 0,
+            "timing": f"CUDA events; batched: mean of {k} calls after one warm-up; sequential: one pass "
+                      "after 64 warm-up calls; inputs resident in HBM"}
+
+
+def bench_serving(vq, torch, nreq, budget=40 << 30, lanes=3):
+    """Continuous-batching server vs one vq_hull2d_host call per request, on
+    the same Poisson arrivals, at rates up to past the plain path's
+    saturation."""
+    import threading
+    reqs = synth.serving_requests(nreq, rate_per_s=1.0)  # arrival times at rate 1; scaled per rate
+    pts = [synth.points(r["dist"], r["n"], r["seed"], workers=WORKERS) for r in reqs]
+    cap = max(r["n"] for r in reqs)
+    hbuf = np.empty(cap, dtype=np.int32)
+
+    def plain(rate):
+        """One blocking vq_hull2d_host call per request in arrival order;
+        latency = completion - arrival.  rate None: all arrive at once."""
+        lat, hulls = [], []
+        t0 = time.perf_counter()
+        for r, (x, y) in zip(reqs, pts):
+            ta = t0 + (r["t"] / rate if rate else 0.0)
+            d = ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            h = vq.vq_hull2d_host(x, y, hull_idx=hbuf)
+            lat.append(time.perf_counter() - ta)
+            if rate is None:
+                hulls.append(h.copy())
+        return lat, time.perf_counter() - t0, hulls
+
+    def served(rate):
+        """Requests submitted at their arrival times from one thread; results
+        taken in completion order; latency = (submit start - arrival) +
+        the server's submit-to-completion time."""
+        lat = [0.0] * nreq
+        offset = {}
+        hulls = [None] * nreq
+        with vq.Server(mem_budget_bytes=budget, max_inflight=256, lanes=lanes) as srv:
+            t0 = time.perf_counter()
+
+            def submitter():
+                for i, (r, (x, y)) in enumerate(zip(reqs, pts)):
+                    ta = t0 + (r["t"] / rate if rate else 0.0)
+                    d = ta - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    ts = time.perf_counter()
+                    t = srv.submit(x, y)
+                    offset[t] = (i, ts - ta)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            got = []
+            for _ in range(nreq):
+                res = srv.wait_any(cap, timeout_ms=600_000)
+                if res is None:
+                    raise RuntimeError("server: no result within 600 s")
+                got.append(res)
+            th.join()
+            wall = time.perf_counter() - t0
+            info = srv.info()
+        for t, h, ms in got:
+            i, off = offset[t]
+            lat[i] = off + ms / 1e3
+            hulls[i] = h
+        return lat, wall, hulls, info
+
+    def pct(v, q):
+        return float(np.percentile(np.asarray(v) * 1e3, q))
+
+    vq.vq_hull2d_host(*pts[0], hull_idx=hbuf)  # warm-up
+    lat_p, wall_p, hulls_p = plain(None)
+    lat_s, wall_s, hulls_s, info_s = served(None)
+    identical = all(np.array_equal(a, b) for a, b in zip(hulls_p, hulls_s))
+    sat_plain, sat_served = nreq / wall_p, nreq / wall_s
+    sweep = []
+    for f in (0.25, 0.5, 0.9, 1.2):
+        rate = f * sat_plain
+        lp, wp, _ = plain(rate)
+        ls, ws_, _, inf = served(rate)
+        sweep.append({"rate_per_s": rate, "fraction_of_plain_saturation": f,
+                      "plain": {"p50_ms": pct(lp, 50), "p99_ms": pct(lp, 99), "hulls_per_s": nreq / wp},
+                      "served": {"p50_ms": pct(ls, 50), "p99_ms": pct(ls, 99), "hulls_per_s": nreq / ws_,
+                                 "admitted_while_busy": inf["admitted_while_busy"],
+                                 "max_busy_lanes": inf["max_busy_lanes"], "batches": inf["batches"]}})
+    return {"workload": f"{nreq} requests, sizes log-uniform in [100, 1e7] FP64 points, distributions mixed, "
+                        "Poisson arrivals (seed 6); host points (pageable) copied in per request",
+            "points": int(sum(r["n"] for r in reqs)), "budget_bytes": budget, "lanes": lanes,
+            "saturated": {"plain_hulls_per_s": sat_plain, "served_hulls_per_s": sat_served,
+                          "plain_p50_ms": pct(lat_p, 50), "plain_p99_ms": pct(lat_p, 99),
+                          "served_p50_ms": pct(lat_s, 50), "served_p99_ms": pct(lat_s, 99),
+                          "served_peak_bytes": info_s["peak_bytes"], "served_batches": info_s["batches"]},
+            "sweep": sweep, "identical_to_plain_calls": identical}
 
 
 def peaks():
@@ -209,9 +369,9 @@ def main():
         vq.vq_set_config(small_max=args.small_max)
     n = args.n
     if n == FULL_N:
-        data = [synth.workload(d, n) for d in ("square", "disk")]
+        data = [synth.workload(d, n, workers=WORKERS) for d in ("square", "disk")]
     else:
-        data = [synth.points(d, n, synth.WORKLOAD_SEEDS[(d, FULL_N)]) for d in ("square", "disk")]
+        data = [synth.points(d, n, synth.WORKLOAD_SEEDS[(d, FULL_N)], workers=WORKERS) for d in ("square", "disk")]
     dev = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in data]
     outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in dev]
     stream = torch.cuda.current_stream()
@@ -301,6 +461,13 @@ def main():
                "h2d_bytes_per_step": 2 * 16 * n, "d2h_bytes_per_step": 4 * int(sum(hs)),
                "steps": ksteps, "api": "vq_hull2d_host (pinned host buffers)"}
 
+    # batched and serving comparisons (one GPU: reported at N = 1)
+    batched = serving = None
+    if ws == 1 and not args.no_batched:
+        batched = bench_batched(vq, torch, stream, args.steps)
+    if ws == 1 and not args.no_serving:
+        serving = bench_serving(vq, torch, args.serving_requests)
+
     cpu = None
     if rank == 0 and not args.no_cpu and ws == 1:
         m = min(args.cpu_sample, n)
@@ -317,6 +484,7 @@ def main():
                        "l2": "no flush: each input (1.6 GB at 1e8 points) exceeds L2",
                        "parallelism": f"replicas x{ws}", "hull_sizes": hull_sizes},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "batched": batched, "serving": serving,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "tuning": {"points_per_lane": int(vq.vq_get_config().points_per_thread),
                        "small_max": int(vq.vq_get_config().small_max)},

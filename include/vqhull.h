@@ -144,6 +144,13 @@ typedef struct {
                                 (stable, run-to-run identical buffer layout);
                                 0 (default): one atomic per tile (faster; the
                                 hull is identical either way)               */
+  int32_t host_loop;         /* 0 (default): levels >= 1 run as one CUDA graph
+                                launch whose WHILE node repeats the level on
+                                the device until no segment is left (one host
+                                round trip per call instead of one per
+                                level); 1: the host launches every level and
+                                reads its segment count back.  Profiling and
+                                ordered mode always use the host loop.      */
 } vq_config;
 
 vq_status vq_get_config(vq_config* cfg);
@@ -175,6 +182,7 @@ typedef struct {
   double k3_ms;              /* small-segment finisher                        */
   double k4_ms;              /* ordering                                      */
   double other_ms;           /* scans, tile maps, counter resets              */
+  int64_t graph_launches;    /* level loops run as a device-driven graph      */
 } vq_profile;
 
 vq_status vq_profile_read(vq_profile* out, int32_t reset);
@@ -189,11 +197,24 @@ typedef struct {
   size_t mem_budget_bytes; /* device memory the server may use in total      */
   int32_t max_inflight;    /* requests resident on the device at once (>= 1) */
   int32_t device;          /* CUDA device ordinal                            */
+  int32_t lanes;           /* batches on the device at once, each on its own
+                              stream (1..16; 0 = default 3)                   */
 } vq_server_config;
 
-/* Creates a server with its own device pool and a host thread that admits
- * queued requests as memory frees up and advances all resident requests
- * together, one partition level per step. */
+/*
+ * Creates a server: continuous batching of hull requests (the level-
+ * synchronous extraction of Sec. 3 applied to many requests at once).
+ * Each of `lanes` host threads owns a CUDA stream and a hull context.  An
+ * idle lane takes the queued requests (FIFO) that fit the free request
+ * slots (max_inflight) and the free device memory (mem_budget_bytes),
+ * copies their points in and runs them as one batched level-synchronous
+ * hull, so that all segments of its requests share every level step.
+ * Requests that arrive while other batches are on the GPU are admitted by
+ * another lane as soon as slots and memory allow, and their kernels overlap
+ * with the running batches on the device.  Device memory comes from a pool
+ * owned by the server; the admitted requests' bytes (points, outputs and
+ * the exact workspace of their batch) never exceed the budget.
+ */
 vq_status vq_server_create(const vq_server_config* cfg, vq_server** out);
 
 /* Queues a hull of n host points (copied before return; the caller may free
@@ -210,8 +231,30 @@ vq_status vq_server_poll(vq_server* s, uint64_t ticket, int32_t* hull_idx_host, 
 vq_status vq_server_wait(vq_server* s, uint64_t ticket, int32_t* hull_idx_host, int64_t cap, int64_t* h,
                          int32_t timeout_ms);
 
+/* Waits up to timeout_ms (< 0: no limit) for any request to finish and takes
+ * the one that finished first among those not yet taken: *ticket, *h and
+ * its result as for vq_server_poll, and *latency_ms (may be NULL) the time
+ * from its submission to its completion on the server's clock.  Returns
+ * VQ_PENDING if none finished in time.  VQ_ERR_CAPACITY (cap < h) sets
+ * *ticket and *h and leaves the result to vq_server_wait / vq_server_poll. */
+vq_status vq_server_wait_any(vq_server* s, uint64_t* ticket, int32_t* hull_idx_host, int64_t cap, int64_t* h,
+                             int32_t timeout_ms, double* latency_ms);
+
 /* Latency percentiles (submit to completion) and throughput so far. */
 vq_status vq_server_stats(vq_server* s, double* p50_ms, double* p99_ms, double* hulls_per_s);
+
+/* Counters of the server since its creation. */
+typedef struct {
+  int64_t completed;            /* requests finished (with any status)           */
+  int64_t batches;              /* batches run                                   */
+  int64_t max_busy_lanes;       /* most lanes running a batch at the same time   */
+  int64_t admitted_while_busy;  /* requests admitted while another lane's batch
+                                   was on the device                            */
+  int64_t peak_bytes;           /* most device bytes held by admitted batches    */
+  int64_t budget_bytes;         /* the configured budget                         */
+} vq_server_info;
+
+vq_status vq_server_info_read(vq_server* s, vq_server_info* out);
 
 /* Stops the server thread and frees its memory; pending requests are dropped. */
 void vq_server_destroy(vq_server* s);

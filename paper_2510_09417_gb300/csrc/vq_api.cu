@@ -24,6 +24,7 @@ struct Config {
   int ordered = 0;
   long long timeout_ns = 2000000000ll;
   int drop_tile = -1;
+  int host_loop = 0;
 };
 
 static std::mutex g_cfg_mu;
@@ -46,6 +47,23 @@ static vq_status cuda_status(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_status(e_);      \
   } while (0)
 
+// A captured device-driven level loop: one CUDA graph whose WHILE node
+// repeats levels >= 1 until no segment is left.  Kernel arguments are fixed
+// at capture, so a graph is reused only for the same workspace layout,
+// inputs and tuning (the key).
+struct LevelGraph {
+  std::vector<unsigned char> key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long used = 0;
+};
+constexpr int kGraphCache = 16;           // graphs kept per device (least recently used goes)
+// Capturing and instantiating a graph costs about as much as a few host
+// round trips, so smaller runs keep the host loop unless their graph is
+// already cached.
+constexpr long long kGraphMinPoints = 1ll << 22;
+constexpr int kGraphKernelsPerIter = 11;  // two levels of 5 kernels, and the condition
+
 struct Ctx {
   std::mutex mu;
   bool init = false;
@@ -53,6 +71,7 @@ struct Ctx {
   int sms = 0;
   char* mem = nullptr;
   size_t bytes = 0;
+  bool external = false;   // mem belongs to the caller (server lanes): never freed or grown here
   Ctrl* h_ctrl = nullptr;  // pinned
   long long* h_total = nullptr;
   // staging for vq_hull2d_host
@@ -74,6 +93,11 @@ struct Ctx {
   vq_profile prof{};
   std::vector<cudaEvent_t> events;
   std::vector<int> ev_kind;  // one entry per (start, stop) pair
+  // device-driven level loop: capture stream and the graph cache
+  cudaStream_t gstream = nullptr;
+  bool graph_off = false;  // a graph could not be built here: host loop from then on
+  std::vector<LevelGraph> graphs;
+  unsigned long long graph_clock = 0;
 };
 
 enum { kKindOther = 0, kKindK0, kKindK1, kKindK2, kKindK3, kKindK4 };
@@ -206,6 +230,7 @@ static vq_status ctx_init(Ctx& c) {
 
 static vq_status ctx_reserve(Ctx& c, size_t bytes) {
   if (bytes <= c.bytes) return VQ_OK;
+  if (c.external) return VQ_ERR_CAPACITY;
   if (c.mem) {
     cudaFree(c.mem);
     c.mem = nullptr;
@@ -224,6 +249,90 @@ static vq_status ctx_reserve(Ctx& c, size_t bytes) {
     return VQ_ERR_NOMEM;
   }
   c.bytes = want;
+  return VQ_OK;
+}
+
+static void graph_free(LevelGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  g.exec = nullptr;
+  g.graph = nullptr;
+}
+
+// Returns the instantiated level-loop graph for `w` (captured on first use).
+// The body is two levels, parity 1 then parity 0, followed by the condition
+// kernel; a level whose segment count is zero does nothing in any of its
+// kernels, so the second level of the last iteration may run empty.  Level
+// numbers passed to the kernels matter only for their parity and for
+// level > 0 (the level-0 kernels read the caller's arrays and run before the
+// graph).  The partition kernel gets its persistent grid: it reads the
+// level's tile count from the control block.
+// With cached_only set, returns VQ_OK and *out = nullptr when no graph for
+// `w` is cached yet.
+static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cached_only, cudaGraphExec_t* out) {
+  *out = nullptr;
+  std::vector<unsigned char> key(sizeof(Work) + 2 * sizeof(int));
+  memcpy(key.data(), &w, sizeof(Work));
+  memcpy(key.data() + sizeof(Work), &cfg.ppt, sizeof(int));
+  memcpy(key.data() + sizeof(Work) + sizeof(int), &c.sms, sizeof(int));
+  for (LevelGraph& g : c.graphs)
+    if (g.key == key) {
+      g.used = ++c.graph_clock;
+      *out = g.exec;
+      return VQ_OK;
+    }
+  if (cached_only) return VQ_OK;
+  if (!c.gstream) VQ_CHECK(cudaStreamCreateWithFlags(&c.gstream, cudaStreamNonBlocking));
+  LevelGraph g;
+  g.key = key;
+  VQ_CHECK(cudaGraphCreate(&g.graph, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g.graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};  // the rest zero
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &p);
+  }
+  if (e == cudaSuccess) {
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c.gstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      const long long before = kernels_launched();
+      const long long max_iters = (long long)w.N / 2 + 4;
+      cudaStream_t gs = c.gstream;
+      for (int level = 1; level <= 2 && e == cudaSuccess; level++) {
+        if (e == cudaSuccess) e = launch_prologue(w, level, gs);
+        if (e == cudaSuccess) e = launch_k1(w, level, cfg.ppt, INT_MAX / 4, gs);
+        if (e == cudaSuccess) e = launch_k2(w, level, c.sms * 8, gs);
+        if (e == cudaSuccess) e = launch_tilemap(w, (level + 1) & 1, c.sms * 4, gs);
+        if (e == cudaSuccess) e = launch_k3(w, c.sms * 2, gs);
+      }
+      if (e == cudaSuccess) e = launch_level_cond(w, h, max_iters, gs);
+      cudaGraph_t captured = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(gs, &captured);
+      if (e == cudaSuccess) e = e2;
+      count_launches(before - kernels_launched());  // capturing launches nothing
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    graph_free(g);
+    return cuda_status(e);
+  }
+  if ((int)c.graphs.size() >= kGraphCache) {
+    size_t lru = 0;
+    for (size_t i = 1; i < c.graphs.size(); i++)
+      if (c.graphs[i].used < c.graphs[lru].used) lru = i;
+    graph_free(c.graphs[lru]);
+    c.graphs.erase(c.graphs.begin() + (long)lru);
+  }
+  g.used = ++c.graph_clock;
+  c.graphs.push_back(g);
+  *out = g.exec;
   return VQ_OK;
 }
 
@@ -278,6 +387,11 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
 
   int level = 0;
   int levels_run = 0;
+  // levels >= 1 on the device (a graph WHILE node) unless the host loop is
+  // asked for, per-kernel events are recorded or offsets come from the
+  // look-back (whose grid is one block per tile)
+  const bool device_loop = !cfg.host_loop && !cfg.profile && !cfg.ordered;
+  bool graph_ran = false;
   // one partition block per tile: level 0 uses the bound (one segment per
   // point set), later levels the count the previous level produced
   long long k1_grid = N / w.tile + nsets + 1;
@@ -293,6 +407,20 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
     levels_run = level + 1;
     if (c.h_ctrl->err & kErrFatal) break;
     if (c.h_ctrl->k1_segs[(level + 1) & 1] == 0) break;
+    if (device_loop && level == 0 && !c.graph_off) {
+      cudaGraphExec_t ex = nullptr;
+      if (level_graph(c, w, cfg, N < kGraphMinPoints, &ex) != VQ_OK) {
+        // nothing was launched: the levels run from the host loop instead
+        c.graph_off = true;
+        ex = nullptr;
+        fprintf(stderr, "vqhull: the device-driven level loop could not be built; using the host loop\n");
+      }
+      if (ex) {
+        VQ_CHECK(cudaGraphLaunch(ex, st));
+        graph_ran = true;
+        break;
+      }
+    }
     k1_grid = c.h_ctrl->k1_tiles[(level + 1) & 1];
     if (level > N + 1) {  // every level removes at least one point per segment
       c.h_ctrl->err |= kErrInternal;
@@ -304,6 +432,13 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   VQ_CHECK(cudaStreamSynchronize(st));
   tm.collect();
+  if (graph_ran) {
+    const long long iters = c.h_ctrl->graph_iters;
+    levels_run = 1 + c.h_ctrl->live_levels;
+    count_launches(iters * kGraphKernelsPerIter);
+    c.prof.k1_launches += 2 * iters;
+    c.prof.graph_launches++;
+  }
   c.prof.calls++;
   c.prof.levels += levels_run;
   c.prof.launches += kernels_launched() - launches0;
@@ -345,6 +480,61 @@ static Ctx* current_ctx(vq_status& s) {
   }
   s = VQ_OK;
   return &g_ctx[dev];
+}
+
+// ---------------------------------------------------------------------------
+// Contexts with caller-provided workspaces (the server's lanes)
+// ---------------------------------------------------------------------------
+
+Ctx* ctx_create() {
+  Ctx* c = new Ctx();
+  if (ctx_init(*c) != VQ_OK) {
+    ctx_destroy(c);
+    return nullptr;
+  }
+  return c;
+}
+
+void ctx_destroy(Ctx* c) {
+  if (!c) return;
+  for (LevelGraph& g : c->graphs) graph_free(g);
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->cev) cudaEventDestroy(e);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->cstream) cudaStreamDestroy(c->cstream);
+  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->mem && !c->external) cudaFree(c->mem);
+  if (c->stage) cudaFree(c->stage);
+  if (c->stage_out) cudaFree(c->stage_out);
+  if (c->mxy) cudaFree(c->mxy);
+  if (c->mid) cudaFree(c->mid);
+  if (c->mout) cudaFree(c->mout);
+  delete c;
+}
+
+size_t batched_workspace_bytes(long long N, int nsets) {
+  const Config cfg = get_cfg();
+  Work w;
+  memset(&w, 0, sizeof w);
+  const long long nkeys = N + nsets;
+  return layout(w, nullptr, N, nsets, nkeys, cfg) + scan_bytes(nkeys, nsets);
+}
+
+vq_status batched_run(Ctx* c, void* workspace, size_t bytes, const double* x, const double* y,
+                      const long long* offsets, int nsets, long long N, int* hull_idx, long long* hull_offsets,
+                      cudaStream_t st) {
+  if (!c || !workspace || !offsets || !hull_offsets || nsets < 1 || N < 0) return VQ_ERR_INVALID_ARG;
+  if (N + nsets > (long long)INT_MAX - 2) return VQ_ERR_TOO_LARGE;
+  if (N > 0 && (!x || !y || !hull_idx)) return VQ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  c->mem = static_cast<char*>(workspace);
+  c->bytes = bytes;
+  c->external = true;
+  const vq_status s = run(*c, x, y, offsets, 0, nsets, N, hull_idx, hull_offsets, nullptr, st);
+  c->mem = nullptr;
+  c->bytes = 0;
+  c->external = false;
+  return s;
 }
 
 }  // namespace vq
@@ -624,6 +814,7 @@ vq_status vq_get_config(vq_config* cfg) {
   cfg->timeout_ns = c.timeout_ns;
   cfg->debug_drop_tile = c.drop_tile;
   cfg->ordered = c.ordered;
+  cfg->host_loop = c.host_loop;
   return VQ_OK;
 }
 
@@ -642,6 +833,7 @@ vq_status vq_set_config(const vq_config* cfg) {
   g_cfg.timeout_ns = cfg->timeout_ns;
   g_cfg.drop_tile = cfg->debug_drop_tile;
   g_cfg.ordered = cfg->ordered ? 1 : 0;
+  g_cfg.host_loop = cfg->host_loop ? 1 : 0;
   return VQ_OK;
 }
 

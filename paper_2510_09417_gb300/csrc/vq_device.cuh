@@ -73,6 +73,10 @@ struct Ctrl {
   unsigned long long k1prof[12];  // profiling builds: partition-kernel cycle and event counters
   unsigned long long k2prof[4];   // profiling builds: finalize counters
   unsigned long long k3prof[8];   // profiling builds: small-segment kernel counters
+  long long graph_iters;    // device-driven level loop: iterations of its body (two levels each)
+  int live_levels;          // levels >= 1 that started with at least one big segment
+  int pad1;
+  unsigned long long loop_t0;  // device-driven level loop: time of its first condition (ns)
 };
 
 // A live segment: points off .. off+len-1 of its source buffer, hull edge

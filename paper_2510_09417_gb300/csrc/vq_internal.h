@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "vq_device.cuh"
+#include "../../include/vqhull.h"
 
 namespace vq {
 
@@ -61,6 +62,8 @@ cudaError_t launch_seed(const Work& w, cudaStream_t st);
 cudaError_t launch_k0(const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st);
 cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st);
+// condition kernel of the device-driven level loop (a graph WHILE node)
+cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, long long max_iters, cudaStream_t st);
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st);
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st);
 cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st);
@@ -77,6 +80,20 @@ cudaError_t scan_exclusive_i64(long long* data, long long n, long long* tmp, cud
 long long scan_tmp_elems(long long n);
 int k1_blocks_per_sm(int ppt);
 long long kernels_launched();  // kernels launched by this library so far (all devices)
+void count_launches(long long k);  // adds k (may be negative) to that count
 int k3_smem_bytes();
+
+// Hull contexts with caller-provided workspaces (vq_api.cu), used by the
+// server: each lane owns a context and runs its batches on its own stream.
+struct Ctx;
+Ctx* ctx_create();  // for the current device; null on failure
+void ctx_destroy(Ctx* c);
+// device bytes a batched run of N points in nsets sets needs (current config)
+size_t batched_workspace_bytes(long long N, int nsets);
+// vq_hull2d_batched with N known on the host and the workspace given
+// (at least batched_workspace_bytes(N, nsets) bytes, 256-byte aligned)
+vq_status batched_run(Ctx* c, void* workspace, size_t bytes, const double* x, const double* y,
+                      const long long* offsets, int nsets, long long N, int* hull_idx, long long* hull_offsets,
+                      cudaStream_t st);
 
 }  // namespace vq

@@ -401,8 +401,38 @@ __global__ void k_prologue(Work w, int level) {
   w.ctrl->k1_segs[par ^ 1] = 0;
   w.ctrl->k1_tiles[par ^ 1] = 0;
   w.ctrl->fill_jobs[par ^ 1] = 0;
-  if (level > 0) w.ctrl->k3_count = 0;
+  if (level > 0) {
+    w.ctrl->k3_count = 0;
+    if (w.ctrl->k1_segs[par] > 0) w.ctrl->live_levels++;
+  }
   w.ctrl->level = level;
+}
+
+// Condition of the device-driven level loop: a CUDA graph WHILE node whose
+// body runs two partition levels (parity 1, then parity 0).  The loop goes
+// on while the next level (parity 1) has segments and no fatal error was
+// raised.  Every level removes at least one point from each of its
+// segments, so max_iters bounds the loop; reaching it is an internal error.
+// A second bound is time: a loop still running kLevelLoopNs after its first
+// condition stops with a timeout (far beyond any real run: a 1e8-point
+// hull-dense input takes under a second).
+constexpr unsigned long long kLevelLoopNs = 60ull * 1000000000ull;
+
+__global__ void k_level_cond(Work w, cudaGraphConditionalHandle h, long long max_iters) {
+  Ctrl* c = w.ctrl;
+  const long long it = ++c->graph_iters;
+  const unsigned long long now = global_ns();
+  if (it == 1) c->loop_t0 = now;
+  bool more = c->k1_segs[1] > 0 && !(c->err & kErrFatal);
+  if (more && it >= max_iters) {
+    c->err |= kErrInternal;
+    more = false;
+  }
+  if (more && now - c->loop_t0 > kLevelLoopNs) {
+    c->err |= kErrTimeout;
+    more = false;
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -1419,6 +1449,14 @@ cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st) {
   k_k0_finalize<<<(unsigned)(blocks > 0 ? blocks : 1), kK0Threads, 0, st>>>(w);
   return cudaGetLastError();
 }
+
+cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, long long max_iters, cudaStream_t st) {
+  count_launch();
+  k_level_cond<<<1, 1, 0, st>>>(w, h, max_iters);
+  return cudaGetLastError();
+}
+
+void count_launches(long long k) { count_launch((int)k); }
 
 cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st) {
   count_launch();

@@ -1,12 +1,16 @@
-// vq_server.cu -- serving handle: hull requests admitted against a device
-// memory budget and run together.
+// vq_server.cu -- serving handle: continuous batching of hull requests.
 //
-// A host thread owns a device pool.  Whenever requests are queued it admits
-// as many as fit (FIFO, up to max_inflight and the memory budget), copies
-// their points into the pool and runs them as one batched level-synchronous
-// hull (all segments of all admitted requests share each level step).  The
-// results are copied back per request; vq_server_poll / vq_server_wait hand
-// them out.
+// Requests are queued by vq_server_submit.  Each lane is a host thread with
+// its own CUDA stream and hull context.  An idle lane takes the queued
+// requests (FIFO) that fit the free request slots and the free device
+// memory, copies their points into memory drawn from the server's pool,
+// and runs them as one batched level-synchronous hull: all segments of all
+// its requests share each level step (Sec. 3's extraction, run for many
+// hulls at once).  Lanes run side by side, so requests that arrive while
+// other batches are on the GPU are admitted as soon as a lane, slots and
+// memory are free, and their kernels overlap with the running batches.
+// Results are copied back per request; vq_server_poll / vq_server_wait hand
+// them out, in any order.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -18,15 +22,15 @@
 #include <vector>
 
 #include "../../include/vqhull.h"
+#include "vq_internal.h"
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// device bytes per point of a request: input (16), ping-pong buffers (40),
-// keys and slots (~5), output (4), tables (~2)
-constexpr double kBytesPerPoint = 68.0;
-constexpr size_t kBytesFixed = 1 << 20;
+constexpr int kDefaultLanes = 3;
+constexpr int kMaxLanes = 16;
+constexpr size_t kBytesFixed = 1 << 20;  // the budget must at least cover this
 
 struct Request {
   uint64_t ticket = 0;
@@ -40,101 +44,168 @@ struct Request {
   Clock::time_point t_done;
 };
 
-size_t request_bytes(int64_t n) { return (size_t)(kBytesPerPoint * (double)n) + 4096; }
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// One batch's device memory, carved from one pool allocation: x and y,
+// the output indices, offsets, hull offsets, then the hull workspace.
+struct BatchLayout {
+  size_t x, y, out, off, hoff, ws, ws_bytes, total;
+};
+
+BatchLayout batch_layout(long long N, int nsets) {
+  BatchLayout L;
+  const size_t n = (size_t)std::max<long long>(N, 1);
+  size_t o = 0;
+  L.x = o;
+  o += align256(sizeof(double) * n);
+  L.y = o;
+  o += align256(sizeof(double) * n);
+  L.out = o;
+  o += align256(sizeof(int32_t) * n);
+  L.off = o;
+  o += align256(sizeof(int64_t) * (size_t)(nsets + 1));
+  L.hoff = o;
+  o += align256(sizeof(int64_t) * (size_t)(nsets + 1));
+  L.ws = o;
+  L.ws_bytes = align256(vq::batched_workspace_bytes(N, nsets));
+  o += L.ws_bytes;
+  L.total = o + 256;  // room to align the pool allocation's start
+  return L;
+}
 
 }  // namespace
 
+struct vq_server;
+
+struct Lane {
+  vq_server* s = nullptr;
+  std::thread thr;
+  cudaStream_t st = nullptr;
+  vq::Ctx* ctx = nullptr;
+};
+
 struct vq_server {
   vq_server_config cfg{};
+  int nlanes = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
   std::map<uint64_t, Request*> all;
+  std::deque<uint64_t> finished;  // tickets in completion order (for vq_server_wait_any)
   uint64_t next_ticket = 1;
   bool stop = false;
-  std::thread thr;
-  // device pool
-  double* d_x = nullptr;
-  double* d_y = nullptr;
-  int32_t* d_out = nullptr;
-  int64_t* d_off = nullptr;
-  int64_t* d_hoff = nullptr;
-  int64_t pool_points = 0;
-  int pool_sets = 0;
-  cudaStream_t stream = nullptr;
-  // stats
+  std::vector<Lane*> lanes;
+  cudaMemPool_t pool = nullptr;
+  // admission state (under mu)
+  long long resident = 0;  // requests admitted and not finished
+  size_t used = 0;         // device bytes of the admitted batches
+  int busy = 0;            // lanes running a batch
+  // statistics (under mu)
   std::vector<double> lat_ms;
   Clock::time_point t_first{};
   Clock::time_point t_last{};
-  long long completed = 0;
-  vq_status fatal = VQ_OK;
+  bool any_submitted = false;
+  vq_server_info info{};
 };
 
-static vq_status ensure_pool(vq_server* s, int64_t points, int sets) {
-  if (points <= s->pool_points && sets <= s->pool_sets) return VQ_OK;
-  cudaFree(s->d_x); cudaFree(s->d_y); cudaFree(s->d_out); cudaFree(s->d_off); cudaFree(s->d_hoff);
-  s->d_x = s->d_y = nullptr; s->d_out = nullptr; s->d_off = s->d_hoff = nullptr;
-  s->pool_points = 0; s->pool_sets = 0;
-  const int64_t P = std::max<int64_t>(points, 1);
-  if (cudaMalloc(&s->d_x, sizeof(double) * P) != cudaSuccess ||
-      cudaMalloc(&s->d_y, sizeof(double) * P) != cudaSuccess ||
-      cudaMalloc(&s->d_out, sizeof(int32_t) * P) != cudaSuccess ||
-      cudaMalloc(&s->d_off, sizeof(int64_t) * (sets + 1)) != cudaSuccess ||
-      cudaMalloc(&s->d_hoff, sizeof(int64_t) * (sets + 1)) != cudaSuccess) {
+// The queue's head can be admitted now (caller holds mu).
+static bool admissible(const vq_server* s) {
+  if (s->queue.empty() || s->resident >= s->cfg.max_inflight) return false;
+  return s->used + batch_layout(s->queue.front()->n, 1).total <= s->cfg.mem_budget_bytes;
+}
+
+// Copies in, runs and copies out one batch on the lane's stream.
+static vq_status run_batch(vq_server* s, Lane* L, const std::vector<Request*>& batch, long long N,
+                           const BatchLayout& B, std::vector<int64_t>& hoff, std::vector<int32_t>& out) {
+  const int ns = (int)batch.size();
+  char* base = nullptr;
+  if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&base), B.total, s->pool, L->st) != cudaSuccess) {
     cudaGetLastError();
     return VQ_ERR_NOMEM;
   }
-  s->pool_points = P;
-  s->pool_sets = sets;
-  return VQ_OK;
+  // every piece of the layout starts on a 256-byte boundary
+  char* mem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~uintptr_t(255));
+  double* dx = reinterpret_cast<double*>(mem + B.x);
+  double* dy = reinterpret_cast<double*>(mem + B.y);
+  int32_t* dout = reinterpret_cast<int32_t*>(mem + B.out);
+  int64_t* doff = reinterpret_cast<int64_t*>(mem + B.off);
+  int64_t* dhoff = reinterpret_cast<int64_t*>(mem + B.hoff);
+  std::vector<int64_t> offs(ns + 1, 0);
+  for (int i = 0; i < ns; i++) offs[i + 1] = offs[i] + batch[i]->n;
+  vq_status st = VQ_OK;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < ns && e == cudaSuccess; i++) {
+    if (batch[i]->n == 0) continue;
+    e = cudaMemcpyAsync(dx + offs[i], batch[i]->x.data(), sizeof(double) * batch[i]->n, cudaMemcpyHostToDevice,
+                        L->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dy + offs[i], batch[i]->y.data(), sizeof(double) * batch[i]->n, cudaMemcpyHostToDevice,
+                          L->st);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(doff, offs.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, L->st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    st = VQ_ERR_CUDA;
+  } else {
+    st = vq::batched_run(L->ctx, mem + B.ws, B.ws_bytes, dx, dy, reinterpret_cast<const long long*>(doff), ns, N,
+                         dout, reinterpret_cast<long long*>(dhoff), L->st);
+  }
+  if (st == VQ_OK || st == VQ_ERR_NONFINITE) {
+    hoff.assign(ns + 1, 0);
+    e = cudaMemcpyAsync(hoff.data(), dhoff, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost, L->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->st);
+    if (e == cudaSuccess) {
+      out.resize((size_t)std::max<int64_t>(hoff[ns], 1));
+      if (hoff[ns] > 0)
+        e = cudaMemcpyAsync(out.data(), dout, sizeof(int32_t) * hoff[ns], cudaMemcpyDeviceToHost, L->st);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      st = VQ_ERR_CUDA;
+    }
+  }
+  cudaFreeAsync(base, L->st);
+  if (cudaStreamSynchronize(L->st) != cudaSuccess) {
+    cudaGetLastError();
+    if (st == VQ_OK) st = VQ_ERR_CUDA;
+  }
+  return st;
 }
 
-static void serve(vq_server* s) {
+static void lane_main(vq_server* s, Lane* L) {
   cudaSetDevice(s->cfg.device);
-  cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   for (;;) {
     std::vector<Request*> batch;
+    long long N = 0;
+    BatchLayout B{};
     {
       std::unique_lock<std::mutex> g(s->mu);
-      s->cv_work.wait(g, [&] { return s->stop || !s->queue.empty(); });
+      s->cv_work.wait(g, [&] { return s->stop || admissible(s); });
       if (s->stop) break;
-      size_t used = kBytesFixed;
-      while (!s->queue.empty() && (int)batch.size() < s->cfg.max_inflight) {
+      // FIFO from the head while request slots and memory allow
+      while (!s->queue.empty() && s->resident + (long long)batch.size() < s->cfg.max_inflight) {
         Request* r = s->queue.front();
-        const size_t b = request_bytes(r->n);
-        if (!batch.empty() && used + b > s->cfg.mem_budget_bytes) break;
-        used += b;
+        const BatchLayout B2 = batch_layout(N + r->n, (int)batch.size() + 1);
+        if (s->used + B2.total > s->cfg.mem_budget_bytes) break;
         batch.push_back(r);
         s->queue.pop_front();
+        N += r->n;
+        B = B2;
       }
+      if (s->busy > 0) s->info.admitted_while_busy += (long long)batch.size();
+      s->busy++;
+      s->resident += (long long)batch.size();
+      s->used += B.total;
+      s->info.batches++;
+      s->info.max_busy_lanes = std::max<int64_t>(s->info.max_busy_lanes, s->busy);
+      s->info.peak_bytes = std::max<int64_t>(s->info.peak_bytes, (int64_t)s->used);
     }
-    // copy in, run all admitted requests together, copy out
-    int64_t total = 0;
-    std::vector<int64_t> offs(batch.size() + 1, 0);
-    for (size_t i = 0; i < batch.size(); i++) { offs[i] = total; total += batch[i]->n; }
-    offs[batch.size()] = total;
-    vq_status st = ensure_pool(s, total, (int)batch.size());
-    std::vector<int64_t> hoff(batch.size() + 1, 0);
+    // other idle lanes may admit what is left
+    s->cv_work.notify_all();
+    std::vector<int64_t> hoff;
     std::vector<int32_t> out;
-    if (st == VQ_OK) {
-      for (size_t i = 0; i < batch.size(); i++) {
-        if (batch[i]->n == 0) continue;
-        cudaMemcpyAsync(s->d_x + offs[i], batch[i]->x.data(), sizeof(double) * batch[i]->n,
-                        cudaMemcpyHostToDevice, s->stream);
-        cudaMemcpyAsync(s->d_y + offs[i], batch[i]->y.data(), sizeof(double) * batch[i]->n,
-                        cudaMemcpyHostToDevice, s->stream);
-      }
-      cudaMemcpyAsync(s->d_off, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice, s->stream);
-      st = vq_hull2d_batched(s->d_x, s->d_y, s->d_off, (int32_t)batch.size(), s->d_out, s->d_hoff, s->stream);
-      if (st == VQ_OK || st == VQ_ERR_NONFINITE) {
-        cudaMemcpyAsync(hoff.data(), s->d_hoff, sizeof(int64_t) * hoff.size(), cudaMemcpyDeviceToHost, s->stream);
-        cudaStreamSynchronize(s->stream);
-        out.resize((size_t)std::max<int64_t>(hoff.back(), 1));
-        if (hoff.back() > 0)
-          cudaMemcpyAsync(out.data(), s->d_out, sizeof(int32_t) * hoff.back(), cudaMemcpyDeviceToHost, s->stream);
-        if (cudaStreamSynchronize(s->stream) != cudaSuccess) st = VQ_ERR_CUDA;
-      }
-    }
+    const vq_status st = run_batch(s, L, batch, N, B, hoff, out);
     const auto now = Clock::now();
     {
       std::lock_guard<std::mutex> g(s->mu);
@@ -148,52 +219,114 @@ static void serve(vq_server* s) {
         } else {
           r->status = st;
         }
-        r->x.clear(); r->x.shrink_to_fit();
-        r->y.clear(); r->y.shrink_to_fit();
+        r->x.clear();
+        r->x.shrink_to_fit();
+        r->y.clear();
+        r->y.shrink_to_fit();
         r->done = true;
         r->t_done = now;
+        s->finished.push_back(r->ticket);
         s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
-        s->completed++;
+        s->info.completed++;
         s->t_last = now;
       }
+      s->busy--;
+      s->resident -= (long long)batch.size();
+      s->used -= B.total;
     }
     s->cv_done.notify_all();
+    s->cv_work.notify_all();
   }
-  cudaStreamDestroy(s->stream);
+}
+
+static void server_free(vq_server* s) {
+  for (Lane* L : s->lanes) {
+    if (L->ctx) vq::ctx_destroy(L->ctx);
+    if (L->st) cudaStreamDestroy(L->st);
+    delete L;
+  }
+  s->lanes.clear();
+  if (s->pool) cudaMemPoolDestroy(s->pool);
+  s->pool = nullptr;
+  for (auto& kv : s->all) delete kv.second;
+  s->all.clear();
+  delete s;
 }
 
 extern "C" {
 
 vq_status vq_server_create(const vq_server_config* cfg, vq_server** out) {
-  if (!cfg || !out || cfg->max_inflight < 1 || cfg->mem_budget_bytes < kBytesFixed) return VQ_ERR_INVALID_ARG;
+  if (!cfg || !out || cfg->max_inflight < 1 || cfg->mem_budget_bytes < kBytesFixed || cfg->lanes < 0 ||
+      cfg->lanes > kMaxLanes)
+    return VQ_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) return VQ_ERR_CUDA;
   if (cfg->device < 0 || cfg->device >= ndev) return VQ_ERR_INVALID_ARG;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(cfg->device) != cudaSuccess) return VQ_ERR_CUDA;
   vq_server* s = new vq_server();
   s->cfg = *cfg;
-  s->thr = std::thread(serve, s);
+  s->nlanes = cfg->lanes > 0 ? cfg->lanes : kDefaultLanes;
+  s->info.budget_bytes = (int64_t)cfg->mem_budget_bytes;
+  vq_status st = VQ_OK;
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof props);
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = cfg->device;
+  if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+    s->pool = nullptr;
+    st = VQ_ERR_CUDA;
+  } else {
+    // freed batches stay cached in the pool up to the budget
+    unsigned long long keep = (unsigned long long)cfg->mem_budget_bytes;
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  for (int i = 0; i < s->nlanes && st == VQ_OK; i++) {
+    Lane* L = new Lane();
+    L->s = s;
+    s->lanes.push_back(L);
+    if (cudaStreamCreateWithFlags(&L->st, cudaStreamNonBlocking) != cudaSuccess) {
+      L->st = nullptr;
+      st = VQ_ERR_CUDA;
+    } else if (!(L->ctx = vq::ctx_create())) {
+      st = VQ_ERR_NOMEM;
+    }
+  }
+  if (st != VQ_OK) {
+    cudaGetLastError();
+    server_free(s);
+    cudaSetDevice(prev);
+    return st;
+  }
+  for (Lane* L : s->lanes) L->thr = std::thread(lane_main, s, L);
+  cudaSetDevice(prev);
   *out = s;
   return VQ_OK;
 }
 
 vq_status vq_server_submit(vq_server* s, const double* x_host, const double* y_host, int64_t n, uint64_t* ticket) {
+  const auto t0 = Clock::now();
   if (!s || !ticket || n < 0 || (n > 0 && (!x_host || !y_host))) return VQ_ERR_INVALID_ARG;
   if (n > (int64_t)INT32_MAX - 2) return VQ_ERR_TOO_LARGE;
-  if (request_bytes(n) + kBytesFixed > s->cfg.mem_budget_bytes) return VQ_ERR_BUDGET;
+  if (batch_layout(n, 1).total + kBytesFixed > s->cfg.mem_budget_bytes) return VQ_ERR_BUDGET;
   Request* r = new Request();
   r->n = n;
   r->x.assign(x_host, x_host + n);
   r->y.assign(y_host, y_host + n);
-  r->t_submit = Clock::now();
+  r->t_submit = t0;
   {
     std::lock_guard<std::mutex> g(s->mu);
     r->ticket = s->next_ticket++;
-    if (s->completed == 0 && s->all.empty()) s->t_first = r->t_submit;
+    if (!s->any_submitted) {
+      s->t_first = t0;
+      s->any_submitted = true;
+    }
     s->all[r->ticket] = r;
     s->queue.push_back(r);
     *ticket = r->ticket;
   }
-  s->cv_work.notify_one();
+  s->cv_work.notify_all();
   return VQ_OK;
 }
 
@@ -233,6 +366,41 @@ vq_status vq_server_wait(vq_server* s, uint64_t ticket, int32_t* hull_idx_host, 
   return take_result(s, ticket, hull_idx_host, cap, h, true, timeout_ms);
 }
 
+vq_status vq_server_wait_any(vq_server* s, uint64_t* ticket, int32_t* hull_idx_host, int64_t cap, int64_t* h,
+                             int32_t timeout_ms, double* latency_ms) {
+  if (!s || !ticket || !h) return VQ_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> g(s->mu);
+  // the oldest finished request that poll / wait have not taken yet
+  auto next = [&]() -> Request* {
+    while (!s->finished.empty()) {
+      auto it = s->all.find(s->finished.front());
+      if (it != s->all.end()) return it->second;
+      s->finished.pop_front();
+    }
+    return nullptr;
+  };
+  Request* r = next();
+  if (!r) {
+    auto pred = [&] { return (r = next()) != nullptr; };
+    if (timeout_ms < 0) s->cv_done.wait(g, pred);
+    else s->cv_done.wait_for(g, std::chrono::milliseconds(timeout_ms), pred);
+  }
+  if (!r) return VQ_PENDING;
+  *ticket = r->ticket;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  *h = (int64_t)r->hull.size();
+  if (r->status == VQ_OK && (cap < *h || (*h > 0 && !hull_idx_host))) {
+    s->finished.pop_front();  // stays available to vq_server_wait / vq_server_poll
+    return VQ_ERR_CAPACITY;
+  }
+  s->finished.pop_front();
+  const vq_status st = r->status;
+  if (st == VQ_OK && *h > 0) memcpy(hull_idx_host, r->hull.data(), sizeof(int32_t) * r->hull.size());
+  s->all.erase(r->ticket);
+  delete r;
+  return st;
+}
+
 vq_status vq_server_stats(vq_server* s, double* p50_ms, double* p99_ms, double* hulls_per_s) {
   if (!s) return VQ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(s->mu);
@@ -247,8 +415,15 @@ vq_status vq_server_stats(vq_server* s, double* p50_ms, double* p99_ms, double* 
   if (p99_ms) *p99_ms = pct(0.99);
   if (hulls_per_s) {
     const double sec = std::chrono::duration<double>(s->t_last - s->t_first).count();
-    *hulls_per_s = (sec > 0.0) ? (double)s->completed / sec : 0.0;
+    *hulls_per_s = (sec > 0.0) ? (double)s->info.completed / sec : 0.0;
   }
+  return VQ_OK;
+}
+
+vq_status vq_server_info_read(vq_server* s, vq_server_info* out) {
+  if (!s || !out) return VQ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  *out = s->info;
   return VQ_OK;
 }
 
@@ -259,11 +434,13 @@ void vq_server_destroy(vq_server* s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->thr.joinable()) s->thr.join();
-  for (auto& kv : s->all) delete kv.second;
+  for (Lane* L : s->lanes)
+    if (L->thr.joinable()) L->thr.join();
+  int prev = 0;
+  const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
   cudaSetDevice(s->cfg.device);
-  cudaFree(s->d_x); cudaFree(s->d_y); cudaFree(s->d_out); cudaFree(s->d_off); cudaFree(s->d_hoff);
-  delete s;
+  server_free(s);
+  if (have_prev) cudaSetDevice(prev);
 }
 
 }  // extern "C"

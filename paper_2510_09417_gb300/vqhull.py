@@ -38,6 +38,7 @@ class Config(ctypes.Structure):
         ("timeout_ns", ctypes.c_int64),
         ("debug_drop_tile", ctypes.c_int32),
         ("ordered", ctypes.c_int32),
+        ("host_loop", ctypes.c_int32),
     ]
 
 
@@ -55,6 +56,7 @@ class Profile(ctypes.Structure):
         ("k3_ms", ctypes.c_double),
         ("k4_ms", ctypes.c_double),
         ("other_ms", ctypes.c_double),
+        ("graph_launches", ctypes.c_int64),
     ]
 
 
@@ -63,13 +65,25 @@ class ServerConfig(ctypes.Structure):
         ("mem_budget_bytes", ctypes.c_size_t),
         ("max_inflight", ctypes.c_int32),
         ("device", ctypes.c_int32),
+        ("lanes", ctypes.c_int32),
+    ]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_int64),
+        ("batches", ctypes.c_int64),
+        ("max_busy_lanes", ctypes.c_int64),
+        ("admitted_while_busy", ctypes.c_int64),
+        ("peak_bytes", ctypes.c_int64),
+        ("budget_bytes", ctypes.c_int64),
     ]
 
 
 SYMBOLS = (
     "vq_status_string", "vq_version", "vq_hull2d", "vq_hull2d_batched", "vq_hull2d_host", "vq_hull2d_noalloc",
     "vq_get_config", "vq_set_config", "vq_last_stats", "vq_profile_read", "vq_server_create", "vq_server_submit",
-    "vq_server_poll", "vq_server_wait", "vq_server_stats", "vq_server_destroy",
+    "vq_server_poll", "vq_server_wait", "vq_server_wait_any", "vq_server_stats", "vq_server_info_read", "vq_server_destroy",
 )
 
 
@@ -121,6 +135,11 @@ def load(build_if_missing: bool = True):
         lib.vq_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]
         lib.vq_server_stats.restype = ctypes.c_int
+        lib.vq_server_wait_any.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), vp, i64, i64p, i32,
+                                           ctypes.POINTER(ctypes.c_double)]
+        lib.vq_server_wait_any.restype = ctypes.c_int
+        lib.vq_server_info_read.argtypes = [vp, ctypes.POINTER(ServerInfo)]
+        lib.vq_server_info_read.restype = ctypes.c_int
         lib.vq_server_destroy.argtypes = [vp]
         lib.vq_server_destroy.restype = None
         _lib = lib
@@ -269,9 +288,9 @@ def vq_profile_read(reset: bool = False) -> dict:
 class Server:
     """vq_server_*: hull requests admitted against a device-memory budget."""
 
-    def __init__(self, mem_budget_bytes: int, max_inflight: int = 64, device: int = 0):
+    def __init__(self, mem_budget_bytes: int, max_inflight: int = 64, device: int = 0, lanes: int = 0):
         self._lib = load()
-        cfg = ServerConfig(mem_budget_bytes, max_inflight, device)
+        cfg = ServerConfig(mem_budget_bytes, max_inflight, device, lanes)
         h = ctypes.c_void_p()
         _check(self._lib.vq_server_create(ctypes.byref(cfg), ctypes.byref(h)), "vq_server_create")
         self._h = h
@@ -302,11 +321,30 @@ class Server:
         _check(st, "vq_server_wait")
         return out[: h.value]
 
+    def wait_any(self, cap: int, timeout_ms: int = -1):
+        """The first finished request not yet taken: (ticket, hull, latency
+        in ms from submission to completion), or None on timeout."""
+        out = np.empty(max(cap, 1), dtype=np.int32)
+        t = ctypes.c_uint64(0)
+        h = ctypes.c_int64(0)
+        lat = ctypes.c_double(0.0)
+        st = self._lib.vq_server_wait_any(self._h, ctypes.byref(t), out.ctypes.data, cap, ctypes.byref(h),
+                                          timeout_ms, ctypes.byref(lat))
+        if st == VQ_PENDING:
+            return None
+        _check(st, "vq_server_wait_any")
+        return int(t.value), out[: h.value], float(lat.value)
+
     def stats(self):
         p50, p99, hps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(self._lib.vq_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(hps)),
                "vq_server_stats")
         return {"p50_ms": p50.value, "p99_ms": p99.value, "hulls_per_s": hps.value}
+
+    def info(self) -> dict:
+        p = ServerInfo()
+        _check(self._lib.vq_server_info_read(self._h, ctypes.byref(p)), "vq_server_info_read")
+        return {name: getattr(p, name) for name, _ in ServerInfo._fields_}
 
     def close(self):
         if self._h:

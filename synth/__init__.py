@@ -20,6 +20,7 @@ paper uses (Sec. 5.4).
 from __future__ import annotations
 
 import math
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -97,29 +98,36 @@ def _fill(dist: str, seed: int, x: np.ndarray, y: np.ndarray, start: int) -> Non
 
 
 def points(dist: str, n: int, seed: int, out_x: np.ndarray | None = None,
-           out_y: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray]:
+           out_y: np.ndarray | None = None, workers: int = 1) -> tuple[np.ndarray, np.ndarray]:
     """n FP64 points of `dist` as two contiguous arrays (x, y).
 
     square: (u, u') in [0,1)^2.  disk: r = sqrt(u), theta = 2*pi*u'.
     circle: (cos theta, sin theta), theta = 2*pi*u.
     kuzmin: r = sqrt(1/(1-u)^2 - 1), theta = 2*pi*u'.
+    workers > 1 fills chunks on that many threads (numpy releases the GIL in
+    its array loops); every value depends only on its index, so the output
+    is the same for any worker count.
     """
     n = int(n)
     x = np.empty(n, dtype=np.float64) if out_x is None else out_x
     y = np.empty(n, dtype=np.float64) if out_y is None else out_y
-    for s in range(0, n, _CHUNK):
-        e = min(n, s + _CHUNK)
-        _fill(dist, seed, x[s:e], y[s:e], s)
+    starts = range(0, n, _CHUNK)
+    if workers > 1 and n > _CHUNK:
+        with ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(lambda s: _fill(dist, seed, x[s:min(n, s + _CHUNK)], y[s:min(n, s + _CHUNK)], s), starts))
+    else:
+        for s in starts:
+            _fill(dist, seed, x[s:min(n, s + _CHUNK)], y[s:min(n, s + _CHUNK)], s)
     return x, y
 
 
-def workload(dist: str, n: int) -> tuple[np.ndarray, np.ndarray]:
+def workload(dist: str, n: int, workers: int = 1) -> tuple[np.ndarray, np.ndarray]:
     """One of the named single-hull workloads with its fixed seed."""
-    return points(dist, n, WORKLOAD_SEEDS[(dist, int(n))])
+    return points(dist, n, WORKLOAD_SEEDS[(dist, int(n))], workers=workers)
 
 
 def batched_sets(nsets: int = 4096, lo: int = 64, hi: int = 1_000_000,
-                 seed: int = BATCHED_SEED):
+                 seed: int = BATCHED_SEED, workers: int = 1):
     """Independent sets with sizes log-uniform in [lo, hi].
 
     Set s has size round(exp(ln lo + u * ln(hi/lo))) and a distribution drawn
@@ -136,9 +144,17 @@ def batched_sets(nsets: int = 4096, lo: int = 64, hi: int = 1_000_000,
     total = int(offsets[-1])
     x = np.empty(total, dtype=np.float64)
     y = np.empty(total, dtype=np.float64)
-    for s in range(nsets):
+
+    def fill(s):
         a, b = int(offsets[s]), int(offsets[s + 1])
         points(dists[s], b - a, (seed << 20) + s, x[a:b], y[a:b])
+
+    if workers > 1:
+        with ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(fill, range(nsets)))
+    else:
+        for s in range(nsets):
+            fill(s)
     return x, y, offsets, dists
 
 

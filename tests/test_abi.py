@@ -72,3 +72,7 @@ def test_server_rejects_bad_config(lib):
     assert lib.vq_server_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
     cfg = v.vqhull.ServerConfig(1 << 30, 0, 0)
     assert lib.vq_server_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
+    cfg = v.vqhull.ServerConfig(1 << 30, 4, 0, 17)   # more lanes than allowed
+    assert lib.vq_server_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
+    cfg = v.vqhull.ServerConfig(1 << 30, 4, 0, -1)
+    assert lib.vq_server_create(ctypes.byref(cfg), ctypes.byref(out)) == -1

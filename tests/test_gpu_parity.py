@@ -238,3 +238,42 @@ def test_extreme_ties_within_pairs(vq, shift):
     for s in range(3):
         a, b = offs[s], offs[s + 1]
         assert np.array_equal(hi[ho[s]:ho[s + 1]], oracle.hull(x[a:b], y[a:b])), s
+
+
+@pytest.mark.parametrize("dist,n", [("disk", 5_000_000), ("circle", 4_194_304), ("square", 6_000_001)])
+def test_device_level_loop(vq, dist, n):
+    """Levels >= 1 as one CUDA graph launch (a WHILE node repeating two
+    levels on the device) give the same hull and per-level counts as the
+    host-driven loop, and as the oracle; repeated calls reuse the graph."""
+    x, y = synth.points(dist, n, 41)
+    vq.vq_set_config(host_loop=1)
+    vq.vq_profile_read(reset=True)
+    ref = check(vq, x, y, stats=dist != "circle")
+    ref_stats = vq.vq_last_stats()
+    assert vq.vq_profile_read()["graph_launches"] == 0
+    vq.vq_set_config(host_loop=0)
+    for _ in range(2):
+        vq.vq_profile_read(reset=True)
+        got = gpu_hull(vq, x, y)
+        p = vq.vq_profile_read()
+        assert p["graph_launches"] == 1
+        assert np.array_equal(got, ref)
+        assert vq.vq_last_stats() == ref_stats
+    if dist == "circle":
+        code, bad = oracle.verify(x, y, got)
+        assert code == 0, (oracle.VERIFY_CODES.get(code), bad)
+
+
+def test_device_level_loop_batched(vq):
+    """The batched path through the device-driven level loop: every set's
+    hull equals the oracle's."""
+    x, y, offs, dists = synth.batched_sets(nsets=64, lo=2000, hi=1_000_000, seed=43)
+    assert offs[-1] >= 1 << 22
+    vq.vq_profile_read(reset=True)
+    hi, ho = vq.vq_hull2d_batched(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(),
+                                  torch.from_numpy(offs).cuda())
+    assert vq.vq_profile_read()["graph_launches"] == 1
+    hi, ho = hi.cpu().numpy(), ho.cpu().numpy()
+    for s in range(64):
+        a, b = offs[s], offs[s + 1]
+        assert np.array_equal(hi[ho[s]:ho[s + 1]], oracle.hull(x[a:b], y[a:b])), s

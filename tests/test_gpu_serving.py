@@ -58,6 +58,38 @@ def test_server_matches_oracle(vq):
     assert 0 < st["p50_ms"] <= st["p99_ms"]
 
 
+def test_server_continuous_batching(vq):
+    """Requests that arrive while another batch is on the GPU are admitted by
+    another lane at once (not after the running batch), finish before it,
+    and each result is the same as the request's hull computed alone (and
+    the oracle's)."""
+    big = synth.points("circle", 20_000_000, 51)   # hull-dense: its batch runs for a while
+    small = [synth.points(synth.DISTRIBUTIONS[i % 4], 1000 + 4321 * i, 60 + i) for i in range(20)]
+    budget = 4 << 30
+    with vq.Server(mem_budget_bytes=budget, max_inflight=64, lanes=3) as srv:
+        tb = srv.submit(*big)
+        time.sleep(0.02)
+        ts = [srv.submit(x, y) for x, y in small]
+        got = [srv.wait(t, len(p[0]), timeout_ms=120_000) for t, p in zip(ts, small)]
+        big_pending_after_small = srv.poll(tb, len(big[0])) is None
+        got_big = srv.wait(tb, len(big[0]), timeout_ms=120_000) if big_pending_after_small else None
+        info = srv.info()
+    assert info["admitted_while_busy"] >= 1
+    assert info["max_busy_lanes"] >= 2
+    assert info["batches"] >= 2
+    assert 0 < info["peak_bytes"] <= budget
+    assert info["completed"] == 21
+    assert big_pending_after_small
+    for (x, y), g in zip(small, got):
+        alone = vq.vq_hull2d(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).cpu().numpy()
+        assert np.array_equal(g, alone)
+        assert np.array_equal(g, oracle.hull(x, y))
+    alone = vq.vq_hull2d(torch.from_numpy(big[0]).cuda(), torch.from_numpy(big[1]).cuda()).cpu().numpy()
+    assert np.array_equal(got_big, alone)
+    code, bad = oracle.verify(big[0], big[1], got_big)
+    assert code == 0, (oracle.VERIFY_CODES.get(code), bad)
+
+
 def test_server_budget(vq):
     with vq.Server(mem_budget_bytes=64 << 20, max_inflight=4) as srv:
         x, y = synth.points("disk", 2_000_000, 1)  # about 136 MB of device memory: above the budget
