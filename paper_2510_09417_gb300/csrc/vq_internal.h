@@ -12,6 +12,8 @@ namespace vq {
 constexpr int kK1Threads = 128;  // partition block: 4 warps, one tile per block
 constexpr int kK0Threads = 256;
 constexpr int kK0Tile = 32768;      // points per extreme-pass tile
+constexpr int kK0Pairs = 2;         // extreme pass: point pairs per array, thread and stage
+constexpr int kK0Stages = 4;        // extreme pass: shared-memory ring stages (64 KB per block)
 constexpr int kK3Cap = 1024;        // points per warp in the small-segment kernel
 constexpr int kK3Warps = 4;
 constexpr int kK3Stack = 24;

@@ -225,15 +225,33 @@ __device__ __forceinline__ int k0_flags(unsigned long long am) {
   return (am >= 0x7ff0000000000000ull ? 1 : 0) | (am >= 0x4270000000000000ull ? 2 : 0);
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, completion
+// tracked per thread by commit groups).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Lexicographic min and max (x, then y, then lowest index) of each tile and
 // its flags.  Tiles whose first point is 16-byte aligned in both arrays
-// (the usual case) are read as pairs with 16-byte loads, eight pairs per
-// array in flight per thread; others point by point.
+// (the usual case) stream through a ring of kK0Stages shared-memory stages:
+// per stage every thread copies kK0Pairs pairs of x and of y (16 bytes
+// each, consecutive threads on consecutive pairs) with cp.async, and reads
+// back only its own slots, so no barrier is needed between stages; the
+// copies of the next kK0Stages - 1 stages stay in flight while a stage is
+// reduced.  Other tiles are read point by point.
 __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
   __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
   __shared__ int s_fl[kK0Threads / kWarp];
+  extern __shared__ __align__(16) double2 k0_ring[];  // [stage][x|y][pair k][thread]
   const int total = w.k0_tile_start[w.nsets];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int SP = kK0Pairs * kK0Threads;  // pairs per stage
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int lo = 0, hi = w.nsets - 1;
     while (lo < hi) {
@@ -248,30 +266,47 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
     unsigned long long am = 0;
     const bool vec = ((reinterpret_cast<uintptr_t>(w.x + begin) | reinterpret_cast<uintptr_t>(w.y + begin)) & 15u) == 0;
     if (vec) {
-      // pair q covers points 2q, 2q+1; thread tid takes pairs tid + 256 k
+      // pair q covers points 2q, 2q+1; stage i holds pairs i*SP .. i*SP+SP-1
       const double2* px = reinterpret_cast<const double2*>(w.x + begin);
       const double2* py = reinterpret_cast<const double2*>(w.y + begin);
       const int npairs = count >> 1;
-      constexpr int B = 8;
-      for (int q0 = threadIdx.x; q0 < npairs; q0 += B * kK0Threads) {
-        double2 bx[B], by[B];
+      const int nst = (npairs + SP - 1) / SP;
+      auto slot = [&](int st, int a, int k) -> double2* {
+        return k0_ring + ((st * 2 + a) * kK0Pairs + k) * kK0Threads + threadIdx.x;
+      };
+      auto issue = [&](int i) {
+        const int st = i % kK0Stages;
 #pragma unroll
-        for (int k = 0; k < B; k++) {
-          const int q = q0 + k * kK0Threads;
+        for (int k = 0; k < kK0Pairs; k++) {
+          const int q = i * SP + k * kK0Threads + (int)threadIdx.x;
           if (q < npairs) {
-            bx[k] = __ldcs(px + q);
-            by[k] = __ldcs(py + q);
+            cp_async16(slot(st, 0, k), px + q);
+            cp_async16(slot(st, 1, k), py + q);
           }
         }
+      };
 #pragma unroll
-        for (int k = 0; k < B; k++) {
-          const int q = q0 + k * kK0Threads;
+      for (int i = 0; i < kK0Stages - 1; i++) {
+        if (i < nst) issue(i);
+        cp_async_commit();
+      }
+      for (int i = 0; i < nst; i++) {
+        // the slot refilled here was read by this thread in the previous step
+        if (i + kK0Stages - 1 < nst) issue(i + kK0Stages - 1);
+        cp_async_commit();
+        cp_async_wait<kK0Stages - 1>();  // this thread's copies of stage i have landed
+        const int st = i % kK0Stages;
+#pragma unroll
+        for (int k = 0; k < kK0Pairs; k++) {
+          const int q = i * SP + k * kK0Threads + (int)threadIdx.x;
           if (q < npairs) {
-            k0_take(bx[k].x, by[k].x, begin + 2 * q, mn, mx, am);
-            k0_take(bx[k].y, by[k].y, begin + 2 * q + 1, mn, mx, am);
+            const double2 vx = *slot(st, 0, k), vy = *slot(st, 1, k);
+            k0_take(vx.x, vy.x, begin + 2 * q, mn, mx, am);
+            k0_take(vx.y, vy.y, begin + 2 * q + 1, mn, mx, am);
           }
         }
       }
+      cp_async_wait<0>();
       if ((count & 1) && threadIdx.x == 0) k0_take(w.x[begin + count - 1], w.y[begin + count - 1], begin + count - 1, mn, mx, am);
     } else {
 #pragma unroll 8
@@ -609,9 +644,6 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory layout of the partition kernel: an input stage (the tile's
 // points, copied asynchronously) and an output stage (the compacted
@@ -1436,9 +1468,35 @@ cudaError_t launch_seed(const Work& w, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+static int device_sms();
+
+static constexpr int k0_ring_bytes() { return (int)(sizeof(double2) * kK0Stages * 2 * kK0Pairs * kK0Threads); }
+
+// Extreme pass: a resident grid, sized so that every block gets the same
+// number of tiles (the tile count is exact for one set, an upper bound for
+// several).
 cudaError_t launch_k0(const Work& w, int grid, cudaStream_t st) {
+  (void)grid;
+  static int occ[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (occ[dev] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_k0, cudaFuncAttributeMaxDynamicSharedMemorySize, k0_ring_bytes());
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_k0, kK0Threads, k0_ring_bytes());
+    if (e != cudaSuccess) return e;
+    occ[dev] = n > 0 ? n : 1;
+  }
+  const long long tiles = w.offsets ? (long long)w.N / kK0Tile + w.nsets : (w.n_single + kK0Tile - 1) / kK0Tile;
+  long long g = (long long)occ[dev] * device_sms();
+  if (tiles < g) g = tiles;
+  if (g < 1) g = 1;
+  const long long rounds = (tiles + g - 1) / g;
+  if (rounds > 0) g = (tiles + rounds - 1) / rounds;
+  if (g < 1) g = 1;
   count_launch();
-  k_k0<<<grid, kK0Threads, 0, st>>>(w);
+  k_k0<<<(unsigned)g, kK0Threads, k0_ring_bytes(), st>>>(w);
   return cudaGetLastError();
 }
 

@@ -63,23 +63,28 @@ def test_server_continuous_batching(vq):
     another lane at once (not after the running batch), finish before it,
     and each result is the same as the request's hull computed alone (and
     the oracle's)."""
-    big = synth.points("circle", 20_000_000, 51)   # hull-dense: its batch runs for a while
+    big = synth.points("circle", 40_000_000, 51)   # hull-dense: its batch runs for a while
     small = [synth.points(synth.DISTRIBUTIONS[i % 4], 1000 + 4321 * i, 60 + i) for i in range(20)]
-    budget = 4 << 30
+    budget = 6 << 30
     with vq.Server(mem_budget_bytes=budget, max_inflight=64, lanes=3) as srv:
         tb = srv.submit(*big)
         time.sleep(0.02)
         ts = [srv.submit(x, y) for x, y in small]
-        got = [srv.wait(t, len(p[0]), timeout_ms=120_000) for t, p in zip(ts, small)]
-        big_pending_after_small = srv.poll(tb, len(big[0])) is None
-        got_big = srv.wait(tb, len(big[0]), timeout_ms=120_000) if big_pending_after_small else None
+        done = [srv.wait_any(len(big[0]), timeout_ms=120_000) for _ in range(21)]
         info = srv.info()
+    assert all(d is not None for d in done)
+    order = [d[0] for d in done]
+    res = {d[0]: d[1] for d in done}
+    assert sorted(order) == sorted([tb] + ts)
     assert info["admitted_while_busy"] >= 1
     assert info["max_busy_lanes"] >= 2
     assert info["batches"] >= 2
     assert 0 < info["peak_bytes"] <= budget
     assert info["completed"] == 21
-    assert big_pending_after_small
+    # the first request to finish is one that arrived after the big one
+    assert order[0] != tb
+    got = [res[t] for t in ts]
+    got_big = res[tb]
     for (x, y), g in zip(small, got):
         alone = vq.vq_hull2d(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).cpu().numpy()
         assert np.array_equal(g, alone)
