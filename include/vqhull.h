@@ -151,6 +151,13 @@ typedef struct {
                                 level); 1: the host launches every level and
                                 reads its segment count back.  Profiling and
                                 ordered mode always use the host loop.      */
+  int32_t prefilter;         /* 1 (default): level 0 drops the points that lie
+                                certainly inside a polygon of input points
+                                found by the extreme pass (the Akl-Toussaint
+                                octagon the paper proposes as its next step,
+                                Sec. 6); the hull is the same, the per-level
+                                counters are not.  0: plain Alg. 1 counts.
+                                Applies to the default partition kernel.    */
 } vq_config;
 
 vq_status vq_get_config(vq_config* cfg);

@@ -25,6 +25,7 @@ struct Config {
   long long timeout_ns = 2000000000ll;
   int drop_tile = -1;
   int host_loop = 0;
+  int prefilter = 1;
 };
 
 static std::mutex g_cfg_mu;
@@ -183,6 +184,7 @@ static size_t layout(Work& w, char* base, long long N, int nsets, long long nkey
   w.slot = reinterpret_cast<int*>(take(sizeof(int) * (nkeys + 1)));
   w.bitmap = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * ((nkeys + 31) / 32 + 1)));
   w.sets = reinterpret_cast<SetRec*>(take(sizeof(SetRec) * nsets));
+  w.oct = reinterpret_cast<OctF*>(take(sizeof(OctF) * nsets));
   w.k0_tile_start = reinterpret_cast<int*>(take(sizeof(int) * (nsets + 1)));
   w.capT0 = (int)(n / kK0Tile + nsets + 1);
   w.k0part = reinterpret_cast<K0Part*>(take(sizeof(K0Part) * w.capT0));
@@ -364,6 +366,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   w.timeout_ns = cfg.timeout_ns;
   w.drop_tile = cfg.drop_tile;
   w.ordered = cfg.ordered;
+  w.prefilter = cfg.prefilter;
   c.d_stats = w.stats;
 
   const long long launches0 = kernels_launched();
@@ -815,6 +818,7 @@ vq_status vq_get_config(vq_config* cfg) {
   cfg->debug_drop_tile = c.drop_tile;
   cfg->ordered = c.ordered;
   cfg->host_loop = c.host_loop;
+  cfg->prefilter = c.prefilter;
   return VQ_OK;
 }
 
@@ -834,6 +838,7 @@ vq_status vq_set_config(const vq_config* cfg) {
   g_cfg.drop_tile = cfg->debug_drop_tile;
   g_cfg.ordered = cfg->ordered ? 1 : 0;
   g_cfg.host_loop = cfg->host_loop ? 1 : 0;
+  g_cfg.prefilter = cfg->prefilter ? 1 : 0;
   return VQ_OK;
 }
 

@@ -38,6 +38,7 @@ constexpr unsigned kErrFatal = kErrTimeout | kErrCapacity | kErrInternal | kErrB
 constexpr int kSegFast = 1;       // FP32 tier allowed (all |coords| < 2^40)
 constexpr int kSegSrcInput = 2;   // points still in the caller's arrays (level 0)
 constexpr int kSegSrcBuf1 = 4;    // points in ping-pong buffer 1 (else buffer 0)
+constexpr int kSegOct = 8;        // level 0: the set's pre-filter chains apply (Work::oct[segment])
 
 // look-back status words: 2 flag bits, 31-bit left count, 31-bit right count
 constexpr unsigned long long kStAgg = 1ull << 62;
@@ -176,6 +177,8 @@ struct K0Part {
   int mini, maxi;
   int flags;  // bit0 nonfinite, bit1 out of FP32 range
   int pad;
+  float ov[6];  // pre-filter directions (see K0Dir), approximate scores
+  int oi[6];    // and the points that reach them
 };
 
 // ---------------------------------------------------------------------------
@@ -511,6 +514,54 @@ __device__ __forceinline__ LineF line1_of(const SegGeom& g) {
 }
 __device__ __forceinline__ LineF line2_of(const SegGeom& g) {
   LineF L; L.ox = g.o2x; L.oy = g.o2y; L.dx = g.d2x; L.dy = g.d2y; L.k = g.k2; L.c = g.c2; return L;
+}
+
+// ---------------------------------------------------------------------------
+// Level-0 pre-filter: the Akl-Toussaint octagon that the paper proposes as
+// its next step (Sec. 6, with the figure of p1..p8).  Per point set, an
+// upper chain p = v0, v1, .., vk = q of input points (x strictly
+// increasing, every inner vertex strictly left of p->q, strict right turns)
+// and a lower chain q, .., p likewise.  The polygon p, upper chain, q is
+// convex and its vertices are input points, so a point strictly inside it
+// is strictly inside the hull: it is never a strict vertex nor a farthest
+// point of any segment, and level 0 drops it before classifying it.  The
+// test (oct_inside) uses the FP32 tier with its bound; every uncertain case
+// keeps the point.
+// ---------------------------------------------------------------------------
+
+struct OctSide {
+  float t[3];   // sx * trunc_f32(x) of the inner vertices in chain order, +inf past the last
+  float sx;     // +1 for the upper chain (x increasing), -1 for the lower chain
+  LineF e[4];   // edge j runs from vertex j to vertex j + 1
+};
+struct OctF {
+  OctSide s[2];  // [0]: upper chain (points left of p->q), [1]: lower chain
+};
+
+// The edge of chain S above (upper) or below (lower) abscissa x, from the
+// truncated x (fx): j with x certainly between the x of vertices j and
+// j + 1 (trunc_f32 is monotone, so fx > t ensures x >= the vertex's x).
+// -1 when fx equals a threshold (x undecided against that vertex).
+__device__ __forceinline__ int oct_edge(const OctSide& S, float fx) {
+  const float v = S.sx * fx;
+  if (v == S.t[0] || v == S.t[1] || v == S.t[2]) return -1;
+  return (v > S.t[0] ? 1 : 0) + (v > S.t[1] ? 1 : 0) + (v > S.t[2] ? 1 : 0);
+}
+
+// The point is certainly strictly inside the polygon p, upper chain, q,
+// lower chain: certainly right of the upper chain's edge over its x and of
+// the lower chain's edge under it.  The polygon is convex (both chains are,
+// and p and q are the extremes in x), so its vertical section at x is the
+// segment between those two edges.
+__device__ __forceinline__ bool oct_inside(const OctF& O, double ux, double uy) {
+  const float fx = trunc_f32(ux), fy = trunc_f32(uy);
+  const int ju = oct_edge(O.s[0], fx), jl = oct_edge(O.s[1], fx);
+  if (ju < 0 || jl < 0) return false;
+  const float m = __fadd_ru(fabsf(fx), fabsf(fy));
+  float du, eu, dl, el;
+  orient_f32(O.s[0].e[ju], fx, fy, m, du, eu);
+  orient_f32(O.s[1].e[jl], fx, fy, m, dl, el);
+  return du < -eu && dl < -el;
 }
 
 // ---------------------------------------------------------------------------

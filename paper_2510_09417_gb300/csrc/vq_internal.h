@@ -14,6 +14,7 @@ constexpr int kK0Threads = 256;
 constexpr int kK0Tile = 32768;      // points per extreme-pass tile
 constexpr int kK0Pairs = 2;         // extreme pass: point pairs per array, thread and stage
 constexpr int kK0Stages = 4;        // extreme pass: shared-memory ring stages (64 KB per block)
+constexpr int kK0OctEvery = 8;      // extreme pass: pre-filter candidates from every 8th stage (power of 2)
 constexpr int kK3Cap = 1024;        // points per warp in the small-segment kernel
 constexpr int kK3Warps = 4;
 constexpr int kK3Stack = 24;
@@ -57,6 +58,8 @@ struct Work {
   int drop_tile;             // test knob: this K1 tile never publishes (-1: none)
   int ordered;               // 1: offsets by decoupled look-back (stable layout); 0: atomic cursors
   int all_fast;              // host's copy of !Ctrl::any_slow: selects the FP32-only partition kernel
+  OctF* oct;                 // per level-0 segment (slot < nsets): pre-filter chains, or null (no pre-filter)
+  int prefilter;             // 1: level 0 drops the points inside the pre-filter chains
 };
 
 // launchers (vq_kernels.cu); all enqueue on `st`

@@ -82,7 +82,7 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 // Register a big segment for the next partition level: a slot, a range of
 // tiles, its geometry and its zeroed cursor; the per-tile map is written by
 // k_tilemap from fill jobs of at most kFillTiles tiles each.
-__device__ void push_k1_warp(const Work& w, int par, SegRec R, int lane) {
+__device__ int push_k1_warp(const Work& w, int par, SegRec R, int lane) {
   const int ntiles = (R.len + w.tile - 1) / w.tile;
   const int njobs = (ntiles + kFillTiles - 1) / kFillTiles;
   int slot = 0, base = 0, job = 0;
@@ -96,13 +96,13 @@ __device__ void push_k1_warp(const Work& w, int par, SegRec R, int lane) {
   job = __shfl_sync(kFull, job, 0);
   if (slot >= w.capS || base > w.capT - ntiles || job > w.capJ - njobs) {
     if (lane == 0) atomicOr(&w.ctrl->err, kErrCapacity);
-    return;
+    return -1;
   }
   R.tile_base = base;
   R.ntiles = ntiles;
   if (!VQ_OK_IDX(w, 3, R.a, 0, w.N) || !VQ_OK_IDX(w, 4, R.b, 0, w.N) || !VQ_OK_IDX(w, 5, R.r, 0, w.N) ||
       !VQ_OK_IDX(w, 6, (long long)R.off + R.len, 1, (long long)w.N + 1))
-    return;
+    return -1;
   if (lane == 0) {
     w.segs[par][slot] = R;
     SegGeom g;
@@ -113,6 +113,7 @@ __device__ void push_k1_warp(const Work& w, int par, SegRec R, int lane) {
     w.fjobs[par][job + i] = make_int4(slot, base + i * kFillTiles, min(kFillTiles, ntiles - i * kFillTiles), 0);
   int* st = reinterpret_cast<int*>(&w.sstate[par][slot]);
   for (int i = lane; i < (int)(sizeof(SegState) / sizeof(int)); i += kWarp) st[i] = 0;
+  return slot;
 }
 
 // The per-tile map of level parity `par`: segment, look-back status word
@@ -225,6 +226,54 @@ __device__ __forceinline__ int k0_flags(unsigned long long am) {
   return (am >= 0x7ff0000000000000ull ? 1 : 0) | (am >= 0x4270000000000000ull ? 2 : 0);
 }
 
+// Candidates of the level-0 pre-filter: the points that maximise six
+// scores of the FP32-truncated coordinates: y - x, y, x + y (upper chain,
+// in chain order), x - y, -y, -x - y (lower chain).  The scores are
+// approximate, and only a sample of the points is scored (every eighth
+// stage of a tile, all points of small sets); the chains built from these
+// points are checked exactly, so any choice of points is safe, and a
+// sample of millions of points lands within a hair of the true extremes.
+// Ties go to the lowest index.
+struct K0Oct {
+  float v[6];
+  int i[6];
+};
+__device__ __forceinline__ void oct_init(K0Oct& o) {
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    o.v[k] = -INFINITY;
+    o.i[k] = INT_MAX;
+  }
+}
+__device__ __forceinline__ void oct_merge(K0Oct& o, int k, float v, int i) {
+  if (v > o.v[k] || (v == o.v[k] && i < o.i[k])) {
+    o.v[k] = v;
+    o.i[k] = i;
+  }
+}
+// points arrive in increasing index order per thread: a strict > keeps the lowest
+__device__ __forceinline__ void oct_take(K0Oct& o, double vx, double vy, int i) {
+  const float fx = trunc_f32(vx), fy = trunc_f32(vy);
+  const float d = __fsub_rn(fy, fx), s = __fadd_rn(fx, fy);
+  const float sc[6] = {d, fy, s, -d, -fy, -s};
+#pragma unroll
+  for (int k = 0; k < 6; k++)
+    if (sc[k] > o.v[k]) {
+      o.v[k] = sc[k];
+      o.i[k] = i;
+    }
+}
+__device__ __forceinline__ void oct_warp_reduce(K0Oct& o) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const float v = __shfl_xor_sync(kFull, o.v[k], m);
+      const int i = __shfl_xor_sync(kFull, o.i[k], m);
+      oct_merge(o, k, v, i);
+    }
+}
+
 // Asynchronous 16-byte global -> shared copies (cp.async, completion
 // tracked per thread by commit groups).
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -248,6 +297,7 @@ __device__ __forceinline__ void cp_async_wait() {
 __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
   __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
   __shared__ int s_fl[kK0Threads / kWarp];
+  __shared__ K0Oct s_oc[kK0Threads / kWarp];
   extern __shared__ __align__(16) double2 k0_ring[];  // [stage][x|y][pair k][thread]
   const int total = w.k0_tile_start[w.nsets];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -264,6 +314,8 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
     const int count = min(kK0Tile, S.len - j * kK0Tile);
     LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
     unsigned long long am = 0;
+    K0Oct oc;
+    oct_init(oc);
     const bool vec = ((reinterpret_cast<uintptr_t>(w.x + begin) | reinterpret_cast<uintptr_t>(w.y + begin)) & 15u) == 0;
     if (vec) {
       // pair q covers points 2q, 2q+1; stage i holds pairs i*SP .. i*SP+SP-1
@@ -303,14 +355,25 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
             const double2 vx = *slot(st, 0, k), vy = *slot(st, 1, k);
             k0_take(vx.x, vy.x, begin + 2 * q, mn, mx, am);
             k0_take(vx.y, vy.y, begin + 2 * q + 1, mn, mx, am);
+            if ((i & (kK0OctEvery - 1)) == 0) {
+              oct_take(oc, vx.x, vy.x, begin + 2 * q);
+              oct_take(oc, vx.y, vy.y, begin + 2 * q + 1);
+            }
           }
         }
       }
       cp_async_wait<0>();
-      if ((count & 1) && threadIdx.x == 0) k0_take(w.x[begin + count - 1], w.y[begin + count - 1], begin + count - 1, mn, mx, am);
+      if ((count & 1) && threadIdx.x == 0) {
+        const int l = begin + count - 1;
+        k0_take(w.x[l], w.y[l], l, mn, mx, am);
+        oct_take(oc, w.x[l], w.y[l], l);
+      }
     } else {
 #pragma unroll 8
-      for (int l = threadIdx.x; l < count; l += kK0Threads) k0_take(w.x[begin + l], w.y[begin + l], begin + l, mn, mx, am);
+      for (int l = threadIdx.x; l < count; l += kK0Threads) {
+        k0_take(w.x[begin + l], w.y[begin + l], begin + l, mn, mx, am);
+        if (((l / (2 * SP)) & (kK0OctEvery - 1)) == 0) oct_take(oc, w.x[begin + l], w.y[begin + l], begin + l);
+      }
     }
     int fl = k0_flags(am);
 #pragma unroll
@@ -320,19 +383,27 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
       if (lex_max_better(b, mx)) mx = b;
       fl |= __shfl_xor_sync(kFull, fl, m);
     }
-    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; }
+    oct_warp_reduce(oc);
+    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; s_oc[warp] = oc; }
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int q = 1; q < kK0Threads / kWarp; q++) {
         if (lex_min_better(s_mn[q], mn)) mn = s_mn[q];
         if (lex_max_better(s_mx[q], mx)) mx = s_mx[q];
         fl |= s_fl[q];
+#pragma unroll
+        for (int k = 0; k < 6; k++) oct_merge(oc, k, s_oc[q].v[k], s_oc[q].i[k]);
       }
       K0Part P;
       P.minx = mn.kx; P.miny = mn.ky; P.mini = mn.i;
       P.maxx = mx.kx; P.maxy = mx.ky; P.maxi = mx.i;
       P.flags = fl;
       P.pad = 0;
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        P.ov[k] = oc.v[k];
+        P.oi[k] = oc.i[k];
+      }
       w.k0part[t] = P;
     }
     __syncthreads();
@@ -342,19 +413,23 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
 // One warp per point set: p, q, the set's flags; emit p; make the level-0
 // segment (a = p, b = p, r = q), whose children are p->q (upper, points left
 // of p->q) and q->p (lower), the two calls of Alg. 1's first line.
-__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl, int lane);
+__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl,
+                              const K0Oct& oc, int lane);
 
 // One block per point set: the set's tile partials are reduced by the whole
 // block, then warp 0 finishes the set.
 __global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
   __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
   __shared__ int s_fl[kK0Threads / kWarp];
+  __shared__ K0Oct s_oc[kK0Threads / kWarp];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int s = blockIdx.x; s < w.nsets; s += gridDim.x) {
     SetRec S = w.sets[s];
     if (S.len == 0) continue;  // uniform across the block
     LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
     int fl = 0;
+    K0Oct oc;
+    oct_init(oc);
 #pragma unroll 4
     for (int t = w.k0_tile_start[s] + threadIdx.x; t < w.k0_tile_start[s + 1]; t += kK0Threads) {
       const K0Part P = w.k0part[t];
@@ -362,6 +437,8 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
       if (lex_min_better(a, mn)) mn = a;
       if (lex_max_better(b, mx)) mx = b;
       fl |= P.flags;
+#pragma unroll
+      for (int k = 0; k < 6; k++) oct_merge(oc, k, P.ov[k], P.oi[k]);
     }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
@@ -370,12 +447,15 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
       if (lex_max_better(b, mx)) mx = b;
       fl |= __shfl_xor_sync(kFull, fl, m);
     }
-    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; }
+    oct_warp_reduce(oc);
+    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; s_oc[warp] = oc; }
     __syncthreads();
     if (warp == 0) {
       mn = lane < kK0Threads / kWarp ? s_mn[lane] : LexPt{LLONG_MAX, LLONG_MAX, INT_MAX};
       mx = lane < kK0Threads / kWarp ? s_mx[lane] : LexPt{LLONG_MIN, LLONG_MIN, INT_MAX};
       fl = lane < kK0Threads / kWarp ? s_fl[lane] : 0;
+      if (lane < kK0Threads / kWarp) oc = s_oc[lane];
+      else oct_init(oc);
 #pragma unroll
       for (int m = 16; m >= 1; m >>= 1) {
         const LexPt a = shfl_lex(mn, m), b = shfl_lex(mx, m);
@@ -383,15 +463,93 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
         if (lex_max_better(b, mx)) mx = b;
         fl |= __shfl_xor_sync(kFull, fl, m);
       }
-      k0_finish_set(w, s, S, mn, mx, fl, lane);
+      oct_warp_reduce(oc);
+      k0_finish_set(w, s, S, mn, mx, fl, oc, lane);
     }
     __syncthreads();  // the shared partials are reused by the next set
   }
 }
 
+// Level-0 pre-filter chains of one point set (see OctF).  Side 0 is the
+// sequence p, c0, c1, c2, q (the candidates extreme in y - x, y, x + y),
+// side 1 is q, c3, c4, c5, p.  Lanes 0..19 evaluate the exact orientation
+// of every ordered triple of positions i < j < k of both sequences; lane 0
+// then builds each chain like one half of Andrew's monotone chain: a
+// candidate is kept if it is strictly left of the side's base line (p->q or
+// q->p) and strictly further along x than the chain's last vertex, after
+// popping vertices that would not make a strict right turn.  Returns (in
+// every lane) whether some chain has an inner vertex; `of` is valid in lane 0.
+__device__ int oct_seq(int side, int pos, int p, int q, const K0Oct& oc) {
+  if (pos == 0) return side ? q : p;
+  if (pos == 4) return side ? p : q;
+  return oc.i[3 * side + pos - 1];
+}
+__device__ __forceinline__ int oct_tri(int i, int j, int k) {  // index of (i < j < k) among the 10 triples of 0..4
+  const int base_i[4] = {0, 6, 9, 10};  // triples starting at i: C(4-i, 2), cumulated
+  const int base_j[5] = {0, 0, 3, 5, 6};
+  return base_i[i] + (base_j[j] - base_j[i + 1]) + (k - j - 1);
+}
+__device__ bool build_oct(const Work& w, int p, int q, const K0Oct& oc, OctF& of, int lane) {
+  int sgn = 0;
+  if (lane < 20) {
+    const int side = lane / 10, t = lane % 10;
+    int ti = 0, tj = 1, tk = 2, c = 0;
+    for (int i = 0; i < 5; i++)
+      for (int j = i + 1; j < 5; j++)
+        for (int k = j + 1; k < 5; k++) {
+          if (c == t) { ti = i; tj = j; tk = k; }
+          c++;
+        }
+    const int a = oct_seq(side, ti, p, q, oc), b = oct_seq(side, tj, p, q, oc), d = oct_seq(side, tk, p, q, oc);
+    if (a >= 0 && a < w.N && b >= 0 && b < w.N && d >= 0 && d < w.N)
+      sgn = orient_sign_slow(w.x[a], w.y[a], w.x[b], w.y[b], w.x[d], w.y[d]);
+  }
+  int tab[20];
+#pragma unroll
+  for (int t = 0; t < 20; t++) tab[t] = __shfl_sync(kFull, sgn, t);
+  int on = 0;
+  if (lane == 0) {
+    for (int side = 0; side < 2; side++) {
+      const int* T = tab + 10 * side;
+      const double sx = side ? -1.0 : 1.0;
+      const double bx = w.x[oct_seq(side, 4, p, q, oc)];
+      int st[5];
+      int n = 0;
+      st[n++] = 0;
+      for (int pos = 1; pos <= 3; pos++) {
+        const int idx = oct_seq(side, pos, p, q, oc);
+        if (idx < 0 || idx >= w.N) continue;
+        if (!(T[oct_tri(0, pos, 4)] < 0)) continue;  // orient(A, B, c) > 0: strictly outside the base line
+        const double cx = w.x[idx], lx = w.x[oct_seq(side, st[n - 1], p, q, oc)];
+        if (!(sx * cx > sx * lx && sx * cx < sx * bx)) continue;
+        while (n >= 2 && T[oct_tri(st[n - 2], st[n - 1], pos)] >= 0) n--;
+        st[n++] = pos;
+      }
+      while (n >= 2 && T[oct_tri(st[n - 2], st[n - 1], 4)] >= 0) n--;
+      st[n++] = 4;
+      const int k = n - 2;  // inner vertices st[1 .. n-2]
+      OctSide& S = of.s[side];
+      S.sx = side ? -1.0f : 1.0f;
+      for (int i = 0; i < 3; i++)
+        S.t[i] = i < k ? S.sx * trunc_f32(w.x[oct_seq(side, st[i + 1], p, q, oc)]) : INFINITY;
+      for (int j = 0; j < 4; j++) {
+        if (j <= k) {
+          const int a = oct_seq(side, st[j], p, q, oc), b = oct_seq(side, st[j + 1], p, q, oc);
+          S.e[j] = make_line(w.x[a], w.y[a], w.x[b], w.y[b]);
+        } else {
+          S.e[j] = LineF{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        }
+      }
+      if (k >= 1) on = 1;
+    }
+  }
+  return __shfl_sync(kFull, on, 0) != 0;
+}
+
 // Warp 0 of the finalize block: p, q and the flags of set s; emit p; make
 // the level-0 segment.
-__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl, int lane) {
+__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl,
+                              const K0Oct& oc, int lane) {
   {
     if (fl & 1) {
       if (lane == 0) {
@@ -425,7 +583,11 @@ __device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, c
     if (S.len <= w.small_max) {
       if (lane == 0) push_k3(w, R);
     } else {
-      push_k1_warp(w, 0, R, lane);
+      OctF of;
+      const bool on = w.oct && w.prefilter && (S.flags & kSegFast) && build_oct(w, p, q, oc, of, lane);
+      if (on) R.flags |= kSegOct;
+      const int slot = push_k1_warp(w, 0, R, lane);
+      if (on && lane == 0 && slot >= 0 && slot < w.nsets) w.oct[slot] = of;
     }
   }
 }

@@ -99,12 +99,14 @@ struct alignas(16) K1Stage {
 };
 static_assert(sizeof(SegGeom) == 96, "SegGeom is bulk-copied as 96 bytes");
 
-// A warp's private region: its stages and their mbarriers.
+// A warp's private region: its stages and their mbarriers, and (level 0)
+// the pre-filter chains of the segment it is working on.
 template <int PPT, int NS>
 struct alignas(16) K1Ring {
   static constexpr int TW = 32 * PPT;
   K1Stage<TW> st[NS];
   unsigned long long full[NS];
+  OctF oct;
 };
 
 // Pass-A classification.  FP32 tier: both lines are evaluated without
@@ -130,6 +132,7 @@ __device__ __forceinline__ int classify_a(const SegGeom& g, const LineF& l1, con
   err = 0.0;
   return classify_filter(g, l1, l2, ux, uy, key, err);
 }
+
 
 // Stage one array.  Elements [0, count) of src (element size ES, src
 // ES-aligned) go to slots sh .. sh+count-1 of dst, sh = (src mod 16) / ES.
@@ -300,7 +303,7 @@ __device__ __forceinline__ void k1w_flush(const Work& w, int par, K1Run& r, int 
 
 template <int PPT, bool SRC_INPUT, bool FAST>
 __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PPT>* __restrict__ sg, int lane,
-                                         K1Run& run, unsigned long long* prof) {
+                                         K1Run& run, unsigned long long* prof, OctF* soct) {
   (void)prof;
   K1_MARK(c0);
   typedef typename KeyOf<FAST>::T K;
@@ -313,12 +316,22 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
   const int* I = sg->i + (sg->m.si & 3);
   const SegGeom* G = &sg->g;
   SegState* ss = &w.sstate[par][sid];
+  // level 0: the segment's pre-filter chains (the tile's flags say whether
+  // it has them; a level-0 segment's slot is below nsets)
+  const bool oct = SRC_INPUT && FAST && (sg->m.flags & kSegOct) != 0 && sid < w.nsets;
   if (sid != run.sid) {
     k1w_flush(w, par, run, lane);
     run.sid = sid;
     run.rb[0] = cand_none<double>();
     run.rb[1] = cand_none<double>();
     run.lf[0] = run.lf[1] = run.hf[0] = run.hf[1] = 0.0f;
+    if (oct) {
+      constexpr int NW = (int)(sizeof(OctF) / sizeof(int));
+      const int* src = reinterpret_cast<const int*>(w.oct + sid);
+      int* dst = reinterpret_cast<int*>(soct);
+      for (int i = lane; i < NW; i += kWarp) dst[i] = __ldcg(src + i);
+      __syncwarp();
+    }
   }
   run.t_last = t;
   if (lane == 0) {  // no record in this tile unless the run ends here
@@ -335,16 +348,43 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
     l1 = line1_of(*G);
     l2 = line2_of(*G);
   }
+  auto account = [&](int k, int c, K key, K err) {
+    const K lo = key_lo(key, err), hi = key_hi(key, err);
+    if (c == 3) und |= 1u << k;
+    if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); }
+    if (c == 2) { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); }
+  };
+  bool filtered = false;
+  if constexpr (SRC_INPUT && FAST) {
+    if (oct) {
+      // level 0 with the pre-filter: the points certainly inside the chain
+      // polygon are dropped first (branch-free), then only the survivors,
+      // a few per lane, are classified
+      unsigned keep = 0;
 #pragma unroll
-  for (int k = 0; k < PPT; k++) {
-    const int l = k * kWarp + lane;
-    if (l < count) {
-      K key, err;
-      const int c = classify_a(*G, l1, l2, X[l], Y[l], key, err);
-      const K lo = key_lo(key, err), hi = key_hi(key, err);
-      if (c == 3) und |= 1u << k;
-      if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); }
-      if (c == 2) { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); }
+      for (int k = 0; k < PPT; k++) {
+        const int l = k * kWarp + lane;
+        if (l < count && !oct_inside(*soct, X[l], Y[l])) keep |= 1u << k;
+      }
+      for (unsigned u = keep; u != 0; u &= u - 1) {
+        const int k = __ffs(u) - 1;
+        const int l = k * kWarp + lane;
+        K key, err;
+        const int c = classify_a(*G, l1, l2, X[l], Y[l], key, err);
+        account(k, c, key, err);
+      }
+      filtered = true;
+    }
+  }
+  if (!filtered) {
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      const int l = k * kWarp + lane;
+      if (l < count) {
+        K key, err;
+        const int c = classify_a(*G, l1, l2, X[l], Y[l], key, err);
+        account(k, c, key, err);
+      }
     }
   }
   // exact tiers for the undecided points (rare)
@@ -545,9 +585,9 @@ __global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Wor
     }
     K1Stage<32 * PPT>* sg = &R->st[s];
     if (ALLFAST || (sg->m.flags & kSegFast))
-      k1w_tile<PPT, SRC_INPUT, true>(w, par, sg, lane, run, prof);
+      k1w_tile<PPT, SRC_INPUT, true>(w, par, sg, lane, run, prof, &R->oct);
     else
-      k1w_tile<PPT, SRC_INPUT, ALLFAST>(w, par, sg, lane, run, prof);
+      k1w_tile<PPT, SRC_INPUT, ALLFAST>(w, par, sg, lane, run, prof, &R->oct);
     __syncwarp();
     K1_MARK(i0);
     if (lane == 0 && t_issue < t_end) {

@@ -39,6 +39,7 @@ class Config(ctypes.Structure):
         ("debug_drop_tile", ctypes.c_int32),
         ("ordered", ctypes.c_int32),
         ("host_loop", ctypes.c_int32),
+        ("prefilter", ctypes.c_int32),
     ]
 
 

@@ -38,6 +38,9 @@ def gpu_hull(vq, x, y):
 
 
 def check(vq, x, y, stats=False):
+    """The hull (with the configured pre-filter) equals the oracle's; with
+    stats, the per-level counters of plain Alg. 1 (pre-filter off, restored
+    afterwards) equal the oracle's too."""
     got = gpu_hull(vq, x, y)
     if stats:
         want, st = oracle.hull(x, y, stats=True)
@@ -46,7 +49,13 @@ def check(vq, x, y, stats=False):
     assert got.shape == want.shape, (got.shape, want.shape)
     assert np.array_equal(got, want)
     if stats:
-        gs = vq.vq_last_stats()
+        pre = vq.vq_get_config().prefilter
+        vq.vq_set_config(prefilter=0)
+        try:
+            assert np.array_equal(gpu_hull(vq, x, y), want)
+            gs = vq.vq_last_stats()
+        finally:
+            vq.vq_set_config(prefilter=pre)
         L = st["levels"]
         assert gs["levels"] == L
         assert gs["read"] == st["read"]
@@ -247,8 +256,9 @@ def test_device_level_loop(vq, dist, n):
     host-driven loop, and as the oracle; repeated calls reuse the graph."""
     x, y = synth.points(dist, n, 41)
     vq.vq_set_config(host_loop=1)
+    check(vq, x, y, stats=dist != "circle")
     vq.vq_profile_read(reset=True)
-    ref = check(vq, x, y, stats=dist != "circle")
+    ref = gpu_hull(vq, x, y)
     ref_stats = vq.vq_last_stats()
     assert vq.vq_profile_read()["graph_launches"] == 0
     vq.vq_set_config(host_loop=0)
@@ -277,3 +287,48 @@ def test_device_level_loop_batched(vq):
     for s in range(64):
         a, b = offs[s], offs[s + 1]
         assert np.array_equal(hi[ho[s]:ho[s + 1]], oracle.hull(x[a:b], y[a:b])), s
+
+
+@pytest.mark.parametrize("dist", synth.DISTRIBUTIONS)
+def test_prefilter(vq, dist):
+    """The level-0 pre-filter (points certainly inside the polygon of the
+    extreme pass's candidates are dropped) leaves every hull unchanged and
+    only removes points: level 0 keeps no more points than plain Alg. 1,
+    and far fewer on the square and the disk, where the polygon covers
+    most of the set.  The later levels see a subset of the plain run's
+    points."""
+    x, y = synth.points(dist, 2_000_000, 77)
+    want = oracle.hull(x, y)
+    vq.vq_set_config(prefilter=0)
+    assert np.array_equal(gpu_hull(vq, x, y), want)
+    plain = vq.vq_last_stats()
+    vq.vq_set_config(prefilter=1)
+    assert np.array_equal(gpu_hull(vq, x, y), want)
+    filt = vq.vq_last_stats()
+    assert filt["read"][0] == plain["read"][0] == 2_000_000
+    assert filt["written"][0] <= plain["written"][0]
+    assert sum(filt["read"]) <= sum(plain["read"])
+    if dist in ("square", "disk"):
+        assert filt["written"][0] < 0.2 * plain["written"][0]
+
+
+def test_prefilter_degenerate_candidates(vq):
+    """Sets whose pre-filter candidates coincide, tie or fall on the base
+    line: points on the hull's edges, a triangle with its interior, a
+    diamond whose diagonal extremes are whole edges, duplicated corners."""
+    rng = np.random.default_rng(12)
+    cases = []
+    t = rng.random(200_000)                       # triangle (0,0), (1,0), (0,1) and its interior
+    u = rng.random(200_000)
+    m = t + u < 1
+    cases.append((np.concatenate([t[m], [0.0, 1.0, 0.0]]), np.concatenate([u[m], [0.0, 0.0, 1.0]])))
+    s = rng.integers(-1000, 1001, 300_000).astype(float)   # diamond |x| + |y| <= 1000 on a lattice
+    r = rng.integers(-1000, 1001, 300_000).astype(float)
+    k = np.abs(s) + np.abs(r) <= 1000
+    cases.append((s[k], r[k]))
+    a, b = rng.random(150_000), rng.random(150_000)      # unit square, corners repeated
+    cases.append((np.concatenate([a, [0, 0, 1, 1, 0, 1]]), np.concatenate([b, [0, 1, 0, 1, 0, 1]])))
+    g = rng.integers(0, 3, (2, 100_000)).astype(float)   # 3x3 grid with heavy duplication
+    cases.append((g[0], g[1]))
+    for x, y in cases:
+        check(vq, x, y)
