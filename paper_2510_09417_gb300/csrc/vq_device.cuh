@@ -221,16 +221,19 @@ __device__ __forceinline__ long long order_key(double v) {
   return b >= 0 ? b : -(b & 0x7fffffffffffffffll);
 }
 
-// FP64 -> FP32 by integer ops: keep the sign, clamp magnitudes below
-// 2^-126 to 2^-126, keep the top 23 fraction bits (truncation), rebias the
-// exponent.  For 2^-126 <= |v| < 2^128 the result is v truncated to 24
-// significant bits: |v~ - v| < 2^-23 |v|.  Below 2^-126, |v~ - v| < 2^-125.
+// FP64 -> FP32 by integer ops: keep the top 23 fraction bits (truncation)
+// and rebias the exponent; magnitudes below 2^-126 become exactly -2^-126
+// (negative v) or +2^-126 (positive v and both zeros).  For
+// 2^-126 <= |v| < 2^128 the result is v truncated to 24 significant bits:
+// |v~ - v| < 2^-23 |v|; below 2^-126, |v~ - v| < 2^-125.  The map is
+// monotone (u <= v implies u~ <= v~), so u~ > v~ implies u > v.
 __device__ __forceinline__ float trunc_f32(double v) {
   const unsigned lo = static_cast<unsigned>(__double2loint(v));
   const unsigned hi = static_cast<unsigned>(__double2hiint(v));
-  const unsigned mag = max(hi & 0x7fffffffu, 0x38100000u);
-  const unsigned f = __funnelshift_l(lo, mag, 3) - 0xC0000000u;  // (1023 - 127) << 23, mod 2^32
-  return __uint_as_float(f | (hi & 0x80000000u));
+  const unsigned a = hi & 0x7fffffffu;
+  const unsigned f = a < 0x38100000u ? 0x00800000u : __funnelshift_l(lo, a, 3) - 0xC0000000u;  // (1023 - 127) << 23
+  const unsigned neg = (a | lo) != 0u ? (hi & 0x80000000u) : 0u;  // -0 maps like +0
+  return __uint_as_float(f | neg);
 }
 
 // Exact FP32 -> FP64 widening by integer operations (GB300's FP64 pipe is
@@ -536,6 +539,11 @@ struct OctSide {
 };
 struct OctF {
   OctSide s[2];  // [0]: upper chain (points left of p->q), [1]: lower chain
+  // An axis-parallel box whose closed extent lies in the closed polygon
+  // (checked exactly), as truncated bounds: trunc_f32(x) > bx0 implies
+  // x > the exact bound, so a point passing the four strict tests is
+  // strictly inside the polygon.  Empty (bx0 = +inf) when none was found.
+  float bx0, bx1, by0, by1;
 };
 
 // The edge of chain S above (upper) or below (lower) abscissa x, from the
@@ -546,6 +554,12 @@ __device__ __forceinline__ int oct_edge(const OctSide& S, float fx) {
   const float v = S.sx * fx;
   if (v == S.t[0] || v == S.t[1] || v == S.t[2]) return -1;
   return (v > S.t[0] ? 1 : 0) + (v > S.t[1] ? 1 : 0) + (v > S.t[2] ? 1 : 0);
+}
+
+// The point is certainly strictly inside the inner box (four compares).
+__device__ __forceinline__ bool oct_in_box(const OctF& O, double ux, double uy) {
+  const float fx = trunc_f32(ux), fy = trunc_f32(uy);
+  return fx > O.bx0 && fx < O.bx1 && fy > O.by0 && fy < O.by1;
 }
 
 // The point is certainly strictly inside the polygon p, upper chain, q,

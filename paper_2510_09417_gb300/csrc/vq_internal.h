@@ -14,7 +14,7 @@ constexpr int kK0Threads = 256;
 constexpr int kK0Tile = 32768;      // points per extreme-pass tile
 constexpr int kK0Pairs = 2;         // extreme pass: point pairs per array, thread and stage
 constexpr int kK0Stages = 4;        // extreme pass: shared-memory ring stages (64 KB per block)
-constexpr int kK0OctEvery = 8;      // extreme pass: pre-filter candidates from every 8th stage (power of 2)
+constexpr int kK0OctEvery = 8;      // extreme pass: pre-filter candidates from every 8th tile of a set (power of 2)
 constexpr int kK3Cap = 1024;        // points per warp in the small-segment kernel
 constexpr int kK3Warps = 4;
 constexpr int kK3Stack = 24;

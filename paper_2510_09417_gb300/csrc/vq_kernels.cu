@@ -210,27 +210,35 @@ __device__ __forceinline__ LexPt shfl_lex(const LexPt& p, int m) {
 // patterns (branch-free selects: the batched loads stay in flight); am
 // keeps the largest magnitude bit pattern seen, from which the flags are
 // derived once (k0_flags).
-__device__ __forceinline__ void k0_take(double vx, double vy, int i, LexPt& mn, LexPt& mx,
-                                        unsigned long long& am) {
-  const LexPt p{order_key(vx), order_key(vy), i};
-  if (lex_min_better(p, mn)) mn = p;
-  if (lex_max_better(p, mx)) mx = p;
-  const unsigned long long ax = (unsigned long long)__double_as_longlong(vx) & 0x7fffffffffffffffull;
-  const unsigned long long ay = (unsigned long long)__double_as_longlong(vy) & 0x7fffffffffffffffull;
-  am = am > ax ? am : ax;
-  am = am > ay ? am : ay;
+__device__ __forceinline__ void k0_take(double vx, double vy, int i, LexPt& mn, LexPt& mx, unsigned& am) {
+  const long long kx = order_key(vx);
+  // the full lexicographic compare only when x reaches the current
+  // extreme (rare after the first points)
+  if (kx <= mn.kx) {
+    const LexPt p{kx, order_key(vy), i};
+    if (lex_min_better(p, mn)) mn = p;
+  }
+  if (kx >= mx.kx) {
+    const LexPt p{kx, order_key(vy), i};
+    if (lex_max_better(p, mx)) mx = p;
+  }
+  const unsigned ax = static_cast<unsigned>(__double2hiint(vx)) & 0x7fffffffu;
+  const unsigned ay = static_cast<unsigned>(__double2hiint(vy)) & 0x7fffffffu;
+  am = max(am, max(ax, ay));
 }
-// bit 0: a coordinate is non-finite; bit 1: some |coordinate| >= 2^40
-// (outside the FP32 tier's range)
-__device__ __forceinline__ int k0_flags(unsigned long long am) {
-  return (am >= 0x7ff0000000000000ull ? 1 : 0) | (am >= 0x4270000000000000ull ? 2 : 0);
+// From the largest high word of |coordinate| seen: bit 0: a coordinate is
+// non-finite (exponent all ones); bit 1: some |coordinate| >= 2^40 (outside
+// the FP32 tier's range).  Both thresholds have a zero low word, so the
+// high words decide them exactly.
+__device__ __forceinline__ int k0_flags(unsigned am) {
+  return (am >= 0x7ff00000u ? 1 : 0) | (am >= 0x42700000u ? 2 : 0);
 }
 
 // Candidates of the level-0 pre-filter: the points that maximise six
 // scores of the FP32-truncated coordinates: y - x, y, x + y (upper chain,
 // in chain order), x - y, -y, -x - y (lower chain).  The scores are
 // approximate, and only a sample of the points is scored (every eighth
-// stage of a tile, all points of small sets); the chains built from these
+// tile of a set, and always its first); the chains built from these
 // points are checked exactly, so any choice of points is safe, and a
 // sample of millions of points lands within a hair of the true extremes.
 // Ties go to the lowest index.
@@ -286,6 +294,65 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// One tile's points through the shared-memory ring (see k_k0); OCT: the
+// tile is sampled for the pre-filter candidates.
+template <bool OCT>
+__device__ __forceinline__ void k0_stream(const Work& w, int begin, int count, LexPt& mn, LexPt& mx, unsigned& am,
+                                          K0Oct& oc) {
+  extern __shared__ __align__(16) double2 k0_ring[];  // [stage][x|y][pair k][thread]
+  constexpr int SP = kK0Pairs * kK0Threads;           // pairs per stage
+  // pair q covers points 2q, 2q+1; stage i holds pairs i*SP .. i*SP+SP-1
+  const double2* px = reinterpret_cast<const double2*>(w.x + begin);
+  const double2* py = reinterpret_cast<const double2*>(w.y + begin);
+  const int npairs = count >> 1;
+  const int nst = (npairs + SP - 1) / SP;
+  auto slot = [&](int st, int a, int k) -> double2* {
+    return k0_ring + ((st * 2 + a) * kK0Pairs + k) * kK0Threads + threadIdx.x;
+  };
+  auto issue = [&](int i) {
+    const int st = i % kK0Stages;
+#pragma unroll
+    for (int k = 0; k < kK0Pairs; k++) {
+      const int q = i * SP + k * kK0Threads + (int)threadIdx.x;
+      if (q < npairs) {
+        cp_async16(slot(st, 0, k), px + q);
+        cp_async16(slot(st, 1, k), py + q);
+      }
+    }
+  };
+#pragma unroll
+  for (int i = 0; i < kK0Stages - 1; i++) {
+    if (i < nst) issue(i);
+    cp_async_commit();
+  }
+  for (int i = 0; i < nst; i++) {
+    // the slot refilled here was read by this thread in the previous step
+    if (i + kK0Stages - 1 < nst) issue(i + kK0Stages - 1);
+    cp_async_commit();
+    cp_async_wait<kK0Stages - 1>();  // this thread's copies of stage i have landed
+    const int st = i % kK0Stages;
+#pragma unroll
+    for (int k = 0; k < kK0Pairs; k++) {
+      const int q = i * SP + k * kK0Threads + (int)threadIdx.x;
+      if (q < npairs) {
+        const double2 vx = *slot(st, 0, k), vy = *slot(st, 1, k);
+        k0_take(vx.x, vy.x, begin + 2 * q, mn, mx, am);
+        k0_take(vx.y, vy.y, begin + 2 * q + 1, mn, mx, am);
+        if (OCT) {
+          oct_take(oc, vx.x, vy.x, begin + 2 * q);
+          oct_take(oc, vx.y, vy.y, begin + 2 * q + 1);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if ((count & 1) && threadIdx.x == 0) {
+    const int l = begin + count - 1;
+    k0_take(w.x[l], w.y[l], l, mn, mx, am);
+    if (OCT) oct_take(oc, w.x[l], w.y[l], l);
+  }
+}
+
 // Lexicographic min and max (x, then y, then lowest index) of each tile and
 // its flags.  Tiles whose first point is 16-byte aligned in both arrays
 // (the usual case) stream through a ring of kK0Stages shared-memory stages:
@@ -298,10 +365,8 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
   __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
   __shared__ int s_fl[kK0Threads / kWarp];
   __shared__ K0Oct s_oc[kK0Threads / kWarp];
-  extern __shared__ __align__(16) double2 k0_ring[];  // [stage][x|y][pair k][thread]
   const int total = w.k0_tile_start[w.nsets];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int SP = kK0Pairs * kK0Threads;  // pairs per stage
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int lo = 0, hi = w.nsets - 1;
     while (lo < hi) {
@@ -313,66 +378,21 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
     const int begin = S.off + j * kK0Tile;
     const int count = min(kK0Tile, S.len - j * kK0Tile);
     LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
-    unsigned long long am = 0;
+    unsigned am = 0;
     K0Oct oc;
     oct_init(oc);
     const bool vec = ((reinterpret_cast<uintptr_t>(w.x + begin) | reinterpret_cast<uintptr_t>(w.y + begin)) & 15u) == 0;
+    // pre-filter candidates from every kK0OctEvery-th tile of a set (its
+    // first tile always)
+    const bool sample = (j & (kK0OctEvery - 1)) == 0;
     if (vec) {
-      // pair q covers points 2q, 2q+1; stage i holds pairs i*SP .. i*SP+SP-1
-      const double2* px = reinterpret_cast<const double2*>(w.x + begin);
-      const double2* py = reinterpret_cast<const double2*>(w.y + begin);
-      const int npairs = count >> 1;
-      const int nst = (npairs + SP - 1) / SP;
-      auto slot = [&](int st, int a, int k) -> double2* {
-        return k0_ring + ((st * 2 + a) * kK0Pairs + k) * kK0Threads + threadIdx.x;
-      };
-      auto issue = [&](int i) {
-        const int st = i % kK0Stages;
-#pragma unroll
-        for (int k = 0; k < kK0Pairs; k++) {
-          const int q = i * SP + k * kK0Threads + (int)threadIdx.x;
-          if (q < npairs) {
-            cp_async16(slot(st, 0, k), px + q);
-            cp_async16(slot(st, 1, k), py + q);
-          }
-        }
-      };
-#pragma unroll
-      for (int i = 0; i < kK0Stages - 1; i++) {
-        if (i < nst) issue(i);
-        cp_async_commit();
-      }
-      for (int i = 0; i < nst; i++) {
-        // the slot refilled here was read by this thread in the previous step
-        if (i + kK0Stages - 1 < nst) issue(i + kK0Stages - 1);
-        cp_async_commit();
-        cp_async_wait<kK0Stages - 1>();  // this thread's copies of stage i have landed
-        const int st = i % kK0Stages;
-#pragma unroll
-        for (int k = 0; k < kK0Pairs; k++) {
-          const int q = i * SP + k * kK0Threads + (int)threadIdx.x;
-          if (q < npairs) {
-            const double2 vx = *slot(st, 0, k), vy = *slot(st, 1, k);
-            k0_take(vx.x, vy.x, begin + 2 * q, mn, mx, am);
-            k0_take(vx.y, vy.y, begin + 2 * q + 1, mn, mx, am);
-            if ((i & (kK0OctEvery - 1)) == 0) {
-              oct_take(oc, vx.x, vy.x, begin + 2 * q);
-              oct_take(oc, vx.y, vy.y, begin + 2 * q + 1);
-            }
-          }
-        }
-      }
-      cp_async_wait<0>();
-      if ((count & 1) && threadIdx.x == 0) {
-        const int l = begin + count - 1;
-        k0_take(w.x[l], w.y[l], l, mn, mx, am);
-        oct_take(oc, w.x[l], w.y[l], l);
-      }
+      if (sample) k0_stream<true>(w, begin, count, mn, mx, am, oc);
+      else k0_stream<false>(w, begin, count, mn, mx, am, oc);
     } else {
 #pragma unroll 8
       for (int l = threadIdx.x; l < count; l += kK0Threads) {
         k0_take(w.x[begin + l], w.y[begin + l], begin + l, mn, mx, am);
-        if (((l / (2 * SP)) & (kK0OctEvery - 1)) == 0) oct_take(oc, w.x[begin + l], w.y[begin + l], begin + l);
+        if (sample) oct_take(oc, w.x[begin + l], w.y[begin + l], begin + l);
       }
     }
     int fl = k0_flags(am);
@@ -508,6 +528,8 @@ __device__ bool build_oct(const Work& w, int p, int q, const K0Oct& oc, OctF& of
 #pragma unroll
   for (int t = 0; t < 20; t++) tab[t] = __shfl_sync(kFull, sgn, t);
   int on = 0;
+  int ev[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // polygon vertices in clockwise order, closed: ev[ne] = ev[0]
+  int ne = 0;
   if (lane == 0) {
     for (int side = 0; side < 2; side++) {
       const int* T = tab + 10 * side;
@@ -527,6 +549,7 @@ __device__ bool build_oct(const Work& w, int p, int q, const K0Oct& oc, OctF& of
       }
       while (n >= 2 && T[oct_tri(st[n - 2], st[n - 1], 4)] >= 0) n--;
       st[n++] = 4;
+      for (int i = 0; i + 1 < n; i++) ev[ne++] = oct_seq(side, st[i], p, q, oc);
       const int k = n - 2;  // inner vertices st[1 .. n-2]
       OctSide& S = of.s[side];
       S.sx = side ? -1.0f : 1.0f;
@@ -542,6 +565,41 @@ __device__ bool build_oct(const Work& w, int p, int q, const K0Oct& oc, OctF& of
       }
       if (k >= 1) on = 1;
     }
+    ev[ne] = ev[0];
+  }
+  // the inner box: x from the larger of the upper-left / lower-left
+  // candidates' x to the smaller of the upper-right / lower-right ones', y
+  // likewise; kept if its four corners lie in the closed polygon (lane k
+  // checks corner k / 8 against edge k % 8 exactly)
+  ne = __shfl_sync(kFull, ne, 0);
+  int efrom = 0, eto = 0;
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    const int f = __shfl_sync(kFull, ev[e], 0), t = __shfl_sync(kFull, ev[e + 1], 0);
+    if ((lane & 7) == e) { efrom = f; eto = t; }
+  }
+  const int iul = oc.i[0], iur = oc.i[2], ilr = oc.i[3], ill = oc.i[5];
+  bool ok = __shfl_sync(kFull, on, 0) != 0 && iul >= 0 && iul < w.N && iur >= 0 && iur < w.N && ilr >= 0 &&
+            ilr < w.N && ill >= 0 && ill < w.N;
+  double bx0 = 0.0, bx1 = 0.0, by0 = 0.0, by1 = 0.0;
+  if (ok) {
+    bx0 = fmax(w.x[iul], w.x[ill]);
+    bx1 = fmin(w.x[iur], w.x[ilr]);
+    by0 = fmax(w.y[ill], w.y[ilr]);
+    by1 = fmin(w.y[iul], w.y[iur]);
+    ok = bx0 < bx1 && by0 < by1;
+  }
+  if (ok && (lane & 7) < ne) {
+    const int corner = lane >> 3;
+    const double cx = (corner == 1 || corner == 2) ? bx1 : bx0, cy = corner >= 2 ? by1 : by0;
+    ok = orient_sign_slow(w.x[efrom], w.y[efrom], w.x[eto], w.y[eto], cx, cy) <= 0;
+  }
+  ok = __all_sync(kFull, ok);
+  if (lane == 0) {
+    of.bx0 = ok ? trunc_f32(bx0) : INFINITY;
+    of.bx1 = ok ? trunc_f32(bx1) : -INFINITY;
+    of.by0 = ok ? trunc_f32(by0) : INFINITY;
+    of.by1 = ok ? trunc_f32(by1) : -INFINITY;
   }
   return __shfl_sync(kFull, on, 0) != 0;
 }

@@ -357,14 +357,27 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
   bool filtered = false;
   if constexpr (SRC_INPUT && FAST) {
     if (oct) {
-      // level 0 with the pre-filter: the points certainly inside the chain
-      // polygon are dropped first (branch-free), then only the survivors,
-      // a few per lane, are classified
-      unsigned keep = 0;
+      // level 0 with the pre-filter: the points certainly inside the inner
+      // box are dropped first (branch-free, four compares), then the rest
+      // are tested against the chain polygon, and only its survivors, a
+      // few per lane, are classified
+      unsigned rest = 0;
+      if (count == TW) {  // full tile: no per-point guard
 #pragma unroll
-      for (int k = 0; k < PPT; k++) {
+        for (int k = 0; k < PPT; k++)
+          if (!oct_in_box(*soct, X[k * kWarp + lane], Y[k * kWarp + lane])) rest |= 1u << k;
+      } else {
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+          const int l = k * kWarp + lane;
+          if (l < count && !oct_in_box(*soct, X[l], Y[l])) rest |= 1u << k;
+        }
+      }
+      unsigned keep = 0;
+      for (unsigned u = rest; u != 0; u &= u - 1) {
+        const int k = __ffs(u) - 1;
         const int l = k * kWarp + lane;
-        if (l < count && !oct_inside(*soct, X[l], Y[l])) keep |= 1u << k;
+        if (!oct_inside(*soct, X[l], Y[l])) keep |= 1u << k;
       }
       for (unsigned u = keep; u != 0; u &= u - 1) {
         const int k = __ffs(u) - 1;
@@ -478,7 +491,7 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
   old = __shfl_sync(kFull, old, 0);
   K1_MARK(c3);
   const long long eL = (long long)(old >> 32), eR = (long long)(old & 0xffffffffull);
-  if (eL + tot0 <= slen && eR + tot1 <= slen) {
+  if (tot0 + tot1 > 0 && eL + tot0 <= slen && eR + tot1 <= slen) {
     const int dstb = par;
     double* __restrict__ dx = w.bx[dstb];
     double* __restrict__ dy = w.by[dstb];
