@@ -51,10 +51,12 @@ UNIT = "Gpoints/s"
 WORKLOAD = "single hulls: uniform square + uniform disk, 1e8 FP64 SoA points each (seeds 1, 2)"
 FULL_N = 100_000_000
 # DRAM bytes the partition kernel moves per algorithmic unit (point
-# classified or kept), from one ncu capture of all partition launches of a
-# 2e7-point disk hull (summarised under profiles/); traffic grows in
-# proportion to the units, so a launch's traffic is this times its units.
-K1_DRAM_BYTES_PER_UNIT = 17.59
+# classified or kept), from one ncu capture of all six partition launches of
+# a 2e7-point disk hull with the level-0 pre-filter on (summarised under
+# profiles/): 456.6 MB read + 30.1 MB written for 26,605,189 points
+# classified and 6,637,667 kept.  Traffic grows in proportion to the units,
+# so a launch's traffic is this times its units.
+K1_DRAM_BYTES_PER_UNIT = 14.64
 
 
 def parse():
@@ -70,6 +72,8 @@ def parse():
                     help="points per workload for the CPU-oracle baseline")
     ap.add_argument("--ppt", type=int, default=0, help="tuning: points per lane of the partition kernel")
     ap.add_argument("--small-max", type=int, default=0, help="tuning: small-segment threshold")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the tuning knobs with vq_autotune on the square workload before timing")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=128)
@@ -375,6 +379,10 @@ def main():
     dev = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in data]
     outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in dev]
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.autotune:
+        cfg, tms = vq.vq_autotune(dev[0][0], dev[0][1], reps=2, stream=stream)
+        tuned = {"autotuned_on": "square workload", "median_ms": tms}
 
     def step():
         hs = []
@@ -437,6 +445,15 @@ def main():
                           f"({ms_prof / args.steps:.3f} ms per step with the events, "
                           f"{ms / args.steps:.3f} ms without)"}
 
+    # the extreme pass against the same peak: 16 bytes read per point
+    k0_bytes = 16.0 * 2 * n * args.steps
+    k0_s = prof["k0_ms"] / 1e3
+    roofline["other_kernels"] = {
+        "k_k0 + k_k0_finalize (extreme pass)": {
+            "achieved": k0_bytes / k0_s / 1e9 if k0_s > 0 else 0.0, "unit": "GB/s",
+            "frac": (k0_bytes / k0_s / 1e9) / peak if k0_s > 0 else 0.0,
+            "ms_per_hull": prof["k0_ms"] / max(prof["calls"], 1)}}
+
     # end to end through the host-buffer entry point (pinned memory)
     e2e = None
     if not args.no_e2e:
@@ -487,7 +504,8 @@ def main():
             "batched": batched, "serving": serving,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "tuning": {"points_per_lane": int(vq.vq_get_config().points_per_thread),
-                       "small_max": int(vq.vq_get_config().small_max)},
+                       "small_max": int(vq.vq_get_config().small_max),
+                       "prefilter": int(vq.vq_get_config().prefilter), "autotune": tuned},
             "detail": {"profile": prof,
                        "paper_model_GBps": (8.0 * 2 * n * args.steps + k1_bytes) / (ms_max / 1e3) / 1e9},
         }

@@ -194,6 +194,23 @@ typedef struct {
 
 vq_status vq_profile_read(vq_profile* out, int32_t reset);
 
+/*
+ * Autotuner of the knobs above for inputs like (x, y, n) (device FP64 SoA,
+ * as for vq_hull2d).  It times the hull of these points on `stream` under
+ * each candidate configuration: points per lane 8 or 16, small-segment
+ * threshold 256 or 1024, level-0 pre-filter on or off.  Every candidate runs
+ * once untimed (workspace, graph capture), then `reps` times (1..16) between
+ * CUDA events.  The fastest by its median time becomes the process-wide
+ * configuration; the other fields keep their current values.
+ *   best     receives that configuration (may be NULL)
+ *   best_ms  receives its median time per hull in ms (may be NULL)
+ * The candidates must agree on the hull's vertex count, else
+ * VQ_ERR_CAPACITY.  The call allocates a temporary device buffer of n
+ * indices and synchronises `stream`.
+ */
+vq_status vq_autotune(const double* x, const double* y, int64_t n, int32_t reps, vq_config* best,
+                      double* best_ms, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Serving: continuous batching of hull requests                        */
 /* ------------------------------------------------------------------ */

@@ -8,6 +8,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -804,6 +805,90 @@ vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, 
     VQ_CHECK(cudaStreamSynchronize(st));
   }
   return s;
+}
+
+vq_status vq_autotune(const double* x, const double* y, int64_t n, int32_t reps, vq_config* best, double* best_ms,
+                      void* stream) {
+  if (n <= 0 || !x || !y || reps < 1 || reps > 16) return VQ_ERR_INVALID_ARG;
+  if (n > (int64_t)INT_MAX - 2) return VQ_ERR_TOO_LARGE;
+  vq_status s;
+  Ctx* c = current_ctx(s);
+  if (!c) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* out = nullptr;
+  if (cudaMalloc(&out, sizeof(int) * (size_t)n) != cudaSuccess) {
+    cudaGetLastError();
+    return VQ_ERR_NOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    cudaFree(out);
+    return VQ_ERR_CUDA;
+  }
+  const Config base = get_cfg();
+  Config win = base;
+  double win_ms = -1.0;
+  long long h0 = -1;
+  vq_status result = VQ_OK;
+  const int ppts[2] = {8, 16}, smalls[2] = {256, 1024}, pres[2] = {0, 1};
+  for (int a = 0; a < 2 && result == VQ_OK; a++)
+    for (int b = 0; b < 2 && result == VQ_OK; b++)
+      for (int d = 0; d < 2 && result == VQ_OK; d++) {
+        Config cand = base;
+        cand.ppt = ppts[a];
+        cand.small_max = smalls[b];
+        cand.prefilter = pres[d];
+        cand.profile = 0;
+        cand.ordered = 0;
+        {
+          std::lock_guard<std::mutex> g(g_cfg_mu);
+          g_cfg = cand;
+        }
+        std::vector<double> ms;
+        for (int r = 0; r <= reps && result == VQ_OK; r++) {
+          long long h = 0;
+          std::lock_guard<std::mutex> g(c->mu);
+          if ((result = ctx_init(*c)) != VQ_OK) break;
+          if (r > 0 && cudaEventRecord(e0, st) != cudaSuccess) result = VQ_ERR_CUDA;
+          if (result == VQ_OK) result = run(*c, x, y, nullptr, n, 1, n, out, nullptr, &h, st);
+          if (result != VQ_OK) break;
+          if (h0 < 0) h0 = h;
+          if (h != h0) {
+            result = VQ_ERR_CAPACITY;
+            break;
+          }
+          if (r > 0) {  // run() synchronised the stream: e1 completes at once
+            float t = 0.f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+              cudaGetLastError();
+              result = VQ_ERR_CUDA;
+              break;
+            }
+            ms.push_back(t);
+          }
+        }
+        if (result != VQ_OK) break;
+        std::sort(ms.begin(), ms.end());
+        const double med = ms[ms.size() / 2];
+        if (win_ms < 0.0 || med < win_ms) {
+          win_ms = med;
+          win = cand;
+        }
+      }
+  {
+    std::lock_guard<std::mutex> g(g_cfg_mu);
+    g_cfg = result == VQ_OK ? win : base;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (result != VQ_OK) return result;
+  if (best) vq_get_config(best);
+  if (best_ms) *best_ms = win_ms;
+  return VQ_OK;
 }
 
 vq_status vq_get_config(vq_config* cfg) {

@@ -83,7 +83,7 @@ class ServerInfo(ctypes.Structure):
 
 SYMBOLS = (
     "vq_status_string", "vq_version", "vq_hull2d", "vq_hull2d_batched", "vq_hull2d_host", "vq_hull2d_noalloc",
-    "vq_get_config", "vq_set_config", "vq_last_stats", "vq_profile_read", "vq_server_create", "vq_server_submit",
+    "vq_get_config", "vq_set_config", "vq_last_stats", "vq_profile_read", "vq_autotune", "vq_server_create", "vq_server_submit",
     "vq_server_poll", "vq_server_wait", "vq_server_wait_any", "vq_server_stats", "vq_server_info_read", "vq_server_destroy",
 )
 
@@ -125,6 +125,8 @@ def load(build_if_missing: bool = True):
         lib.vq_last_stats.restype = ctypes.c_int
         lib.vq_profile_read.argtypes = [ctypes.POINTER(Profile), i32]
         lib.vq_profile_read.restype = ctypes.c_int
+        lib.vq_autotune.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_double), vp]
+        lib.vq_autotune.restype = ctypes.c_int
         lib.vq_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
         lib.vq_server_create.restype = ctypes.c_int
         lib.vq_server_submit.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
@@ -265,6 +267,20 @@ def vq_set_config(cfg: Config | None = None, **kw) -> Config:
         setattr(c, k, v)
     _check(load().vq_set_config(ctypes.byref(c)), "vq_set_config")
     return c
+
+
+def vq_autotune(x: torch.Tensor, y: torch.Tensor, reps: int = 3, stream=None):
+    """Times the hull of (x, y) under each candidate configuration, makes
+    the fastest the process-wide one and returns (config, median ms)."""
+    lib = load()
+    x, y = _dev_f64(x, "x"), _dev_f64(y, "y")
+    if y.shape[0] != x.shape[0]:
+        raise ValueError("x and y differ in length")
+    cfg = Config()
+    ms = ctypes.c_double(0.0)
+    _check(lib.vq_autotune(x.data_ptr(), y.data_ptr(), x.shape[0], reps, ctypes.byref(cfg), ctypes.byref(ms),
+                           _stream_ptr(stream)), "vq_autotune")
+    return cfg, float(ms.value)
 
 
 def vq_last_stats() -> dict:

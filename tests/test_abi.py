@@ -63,6 +63,25 @@ def test_config_validation(lib):
             setattr(c, k, val)
         assert lib.vq_set_config(ctypes.byref(c)) == -1
     assert lib.vq_set_config(ctypes.byref(cfg)) == 0
+    # the level-loop and pre-filter switches round-trip
+    c = v.vq_get_config()
+    c.host_loop, c.prefilter = 1, 0
+    assert lib.vq_set_config(ctypes.byref(c)) == 0
+    got = v.vq_get_config()
+    assert (got.host_loop, got.prefilter) == (1, 0)
+    assert lib.vq_set_config(ctypes.byref(cfg)) == 0
+    assert (v.vq_get_config().host_loop, v.vq_get_config().prefilter) == (cfg.host_loop, cfg.prefilter)
+
+
+def test_autotune_argument_checks(lib):
+    import paper_2510_09417_gb300 as v
+    c = v.vqhull.Config()
+    ms = ctypes.c_double()
+    assert lib.vq_autotune(1, 1, 0, 2, ctypes.byref(c), ctypes.byref(ms), None) == -1
+    assert lib.vq_autotune(None, 1, 10, 2, ctypes.byref(c), ctypes.byref(ms), None) == -1
+    assert lib.vq_autotune(1, 1, 10, 0, ctypes.byref(c), ctypes.byref(ms), None) == -1
+    assert lib.vq_autotune(1, 1, 10, 17, ctypes.byref(c), ctypes.byref(ms), None) == -1
+    assert lib.vq_autotune(1, 1, 2 ** 31, 2, ctypes.byref(c), ctypes.byref(ms), None) == -3
 
 
 def test_server_rejects_bad_config(lib):
