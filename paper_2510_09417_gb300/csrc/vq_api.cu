@@ -878,6 +878,8 @@ vq_status vq_autotune(const double* x, const double* y, int64_t n, int32_t reps,
           win = cand;
         }
       }
+  win.profile = base.profile;  // timed without per-kernel events and look-back; restored
+  win.ordered = base.ordered;
   {
     std::lock_guard<std::mutex> g(g_cfg_mu);
     g_cfg = result == VQ_OK ? win : base;
