@@ -1,0 +1,40 @@
+"""The bench's CPU-side contract: the reference arm (the CPU oracle, as the
+reference) prints one JSON line with the keys the driver reads, and the
+threaded input generation the bench uses gives the same points as the
+single-threaded generator."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "200000",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["unit"] == "Gpoints/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_threaded_generation_is_identical():
+    a = synth.points("kuzmin", (1 << 22) + 12345, 8)
+    b = synth.points("kuzmin", (1 << 22) + 12345, 8, workers=4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    x1, y1, o1, d1 = synth.batched_sets(nsets=40, lo=64, hi=50_000, seed=9)
+    x2, y2, o2, d2 = synth.batched_sets(nsets=40, lo=64, hi=50_000, seed=9, workers=4)
+    assert np.array_equal(o1, o2) and d1 == d2
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2)

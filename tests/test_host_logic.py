@@ -78,3 +78,89 @@ def test_float_widening_bits():
             assert (got >> 52) & 0x7FF == 0x7FF and got & ((1 << 52) - 1), hex(u)
         else:
             assert got == wnt, hex(u)
+
+
+def trunc_f32_bits(v):
+    """The device's FP64 -> FP32 truncation, the same integer construction:
+    top 23 fraction bits kept, exponent rebiased; magnitudes below 2^-126 go
+    to exactly -2^-126 (negative values) or +2^-126 (positive and zeros)."""
+    b = np.asarray(v, dtype=np.float64).view(np.uint64)
+    hi = (b >> np.uint64(32)) & np.uint64(0xffffffff)
+    lo = b & np.uint64(0xffffffff)
+    a = hi & np.uint64(0x7fffffff)
+    shifted = (((a << np.uint64(32)) | lo) >> np.uint64(29)) & np.uint64(0xffffffff)
+    f = np.where(a < np.uint64(0x38100000), np.uint64(0x00800000),
+                 (shifted - np.uint64(0xC0000000)) & np.uint64(0xffffffff))
+    neg = np.where((a | lo) != 0, hi & np.uint64(0x80000000), np.uint64(0))
+    return (f | neg).astype(np.uint32).view(np.float32)
+
+
+def test_truncation_is_monotone_with_its_bound():
+    """The level-0 pre-filter compares truncated coordinates with truncated
+    thresholds and concludes x > t from trunc(x) > trunc(t): that needs the
+    truncation to be monotone, including below 2^-126 and at both zeros.
+    The FP32 tier's bound |v~ - v| <= 2^-23 |v| + 2^-125 must hold too."""
+    rng = np.random.default_rng(3)
+    mags = 10.0 ** rng.uniform(-320, 36, 400_000)
+    vals = np.concatenate([mags * rng.choice([-1.0, 1.0], mags.size),
+                           [0.0, -0.0, 2.0 ** -126, -2.0 ** -126, 2.0 ** -127, -2.0 ** -127,
+                            5e-324, -5e-324, 1.0, -1.0, 2.0 ** 39, -2.0 ** 39]])
+    vals = vals[np.isfinite(vals)]
+    v = np.sort(vals)
+    t = trunc_f32_bits(v).astype(np.float64)
+    assert np.all(np.diff(t) >= 0)
+    assert np.all(np.abs(t - v) <= np.abs(v) * 2.0 ** -23 + 2.0 ** -125)
+    # equal doubles (the two zeros) truncate alike
+    assert trunc_f32_bits(np.array([0.0]))[0] == trunc_f32_bits(np.array([-0.0]))[0]
+    # the contrapositive the filter uses: trunc(x) > trunc(t) implies x > t
+    x = rng.choice(v, 200_000)
+    y = rng.choice(v, 200_000)
+    gt = trunc_f32_bits(x) > trunc_f32_bits(y)
+    assert np.all(x[gt] > y[gt])
+
+
+def test_prefilter_triple_index():
+    """The finalize kernel stores the orientation of the triple (i < j < k)
+    of five chain positions at base_i[i] + base_j[j] - base_j[i + 1] + k - j - 1;
+    that must enumerate the ten triples in lexicographic order."""
+    import itertools
+    base_i = [0, 6, 9, 10]
+    base_j = [0, 0, 3, 5, 6]
+    for t, (i, j, k) in enumerate(itertools.combinations(range(5), 3)):
+        assert base_i[i] + (base_j[j] - base_j[i + 1]) + (k - j - 1) == t
+
+
+def test_strictly_right_of_every_edge_means_strictly_inside():
+    """The lemma behind dropping points at level 0: a point strictly right
+    of every directed edge of a closed polygon (any vertex order, convex or
+    not) lies strictly inside the convex hull of its vertices.  Checked in
+    exact rational arithmetic on random small polygons and random points."""
+    from fractions import Fraction as F
+
+    def orient(a, b, c):
+        v = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+        return (v > 0) - (v < 0)
+
+    def hull_strict_inside(pts, u):
+        # u strictly inside conv(pts) iff for every pair (a, b) with all
+        # points on one closed side, u is strictly on that side
+        n = len(pts)
+        for i in range(n):
+            for j in range(n):
+                if pts[i] == pts[j]:
+                    continue
+                s = [orient(pts[i], pts[j], p) for p in pts]
+                if all(x <= 0 for x in s) and orient(pts[i], pts[j], u) >= 0:
+                    return False
+        return True
+
+    rng = random.Random(5)
+    found = 0
+    for _ in range(8000):
+        k = rng.randint(3, 8)
+        poly = [(F(rng.randint(-6, 6)), F(rng.randint(-6, 6))) for _ in range(k)]
+        u = (F(rng.randint(-12, 12), 2), F(rng.randint(-12, 12), 2))
+        if all(orient(poly[i], poly[(i + 1) % k], u) < 0 for i in range(k)):
+            found += 1
+            assert hull_strict_inside(poly, u), (poly, u)
+    assert found > 50
