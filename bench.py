@@ -83,14 +83,40 @@ def parse():
 WORKERS = max(1, min(16, os.cpu_count() or 1))
 
 
-def bench_batched(vq, torch, stream, steps):
+def cpu_batched_baseline(x, y, offs, max_points=40_000_000):
+    """The oracle on the first sets of the batched workload (at most
+    max_points points in all, at least one set): one oracle hull per set on a
+    thread pool over all host cores (the oracle's C call releases the GIL).
+    Returns the rate of that sample."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.build()
+    sizes = offs[1:] - offs[:-1]
+    k = max(1, int(np.searchsorted(np.cumsum(sizes), max_points, side="right")))
+    pts = int(offs[k])
+    cores = os.cpu_count() or 1
+
+    def one(s):
+        a, b = int(offs[s]), int(offs[s + 1])
+        return oracle.hull(x[a:b], y[a:b]).shape[0]
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(one, range(k)))
+    sec = time.perf_counter() - t0
+    return {"hulls_per_s": k / sec, "gpoints_per_s": pts / sec / 1e9, "cores": cores, "kind": "oracle",
+            "sample": f"the first {k} of the {len(offs) - 1} sets ({pts:,} points), one oracle hull per set "
+                      f"on a pool of {cores} threads", "seconds": sec}
+
+
+def bench_batched(vq, torch, stream, steps, cpu=True):
     """One vq_hull2d_batched call over the 4096-set workload against 4096
-    sequential vq_hull2d calls on the same device-resident sets."""
+    sequential vq_hull2d calls on the same device-resident sets; with cpu,
+    the oracle on a bounded sample of the sets over all host cores."""
     x, y, offs, dists = synth.batched_sets(workers=WORKERS)
     nsets, total = len(offs) - 1, int(offs[-1])
     xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
     od = torch.from_numpy(offs).cuda()
-    del x, y
     hi = torch.empty(total, dtype=torch.int32, device="cuda")
     ho = torch.empty(nsets + 1, dtype=torch.int64, device="cuda")
     vq.vq_hull2d_batched(xd, yd, od, hi, ho, stream=stream)  # warm-up: workspace, graph
@@ -127,12 +153,15 @@ def bench_batched(vq, torch, stream, steps):
     mismatched += int(neq.item() > 0)
     del xd, yd, od, hi, ho, out
     torch.cuda.empty_cache()
+    cpu_base = cpu_batched_baseline(x, y, offs) if cpu else None
+    del x, y
     return {"workload": f"{nsets} sets, sizes log-uniform in [64, 1e6], distributions mixed (seed 5)",
             "sets": nsets, "points": total,
             "batched_ms": ms_batched, "batched_hulls_per_s": nsets / (ms_batched / 1e3),
             "batched_gpoints_per_s": total / (ms_batched / 1e3) / 1e9,
             "sequential_ms": ms_seq, "sequential_hulls_per_s": nsets / (ms_seq / 1e3),
             "speedup": ms_seq / ms_batched, "identical_to_plain_calls": mismatched == 0,
+            "cpu_baseline": cpu_base,
             "timing": f"CUDA events; batched: mean of {k} calls after one warm-up; sequential: one pass "
                       "after 64 warm-up calls; inputs resident in HBM"}
 
@@ -481,7 +510,7 @@ def main():
     # batched and serving comparisons (one GPU: reported at N = 1)
     batched = serving = None
     if ws == 1 and not args.no_batched:
-        batched = bench_batched(vq, torch, stream, args.steps)
+        batched = bench_batched(vq, torch, stream, args.steps, cpu=not args.no_cpu)
     if ws == 1 and not args.no_serving:
         serving = bench_serving(vq, torch, args.serving_requests)
 

@@ -38,3 +38,15 @@ def test_threaded_generation_is_identical():
     x2, y2, o2, d2 = synth.batched_sets(nsets=40, lo=64, hi=50_000, seed=9, workers=4)
     assert np.array_equal(o1, o2) and d1 == d2
     assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
+
+
+def test_cpu_batched_baseline_sample():
+    """The batched section's CPU baseline: a bounded prefix of the sets, each
+    hulled by the oracle on a thread pool."""
+    sys.path.insert(0, ROOT)
+    import bench
+    x, y, offs, _ = synth.batched_sets(nsets=64, lo=64, hi=20_000, seed=4)
+    r = bench.cpu_batched_baseline(x, y, offs, max_points=100_000)
+    k = int(r["sample"].split()[2])
+    assert 1 <= k <= 64 and int(offs[k]) <= 100_000 or k == 1
+    assert r["hulls_per_s"] > 0 and r["cores"] >= 1 and r["kind"] == "oracle"
