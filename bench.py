@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--small-max", type=int, default=0, help="tuning: small-segment threshold")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the tuning knobs with vq_autotune on the square workload before timing")
+    ap.add_argument("--energy-seconds", type=float, default=3.0,
+                    help="seconds of back-to-back steps for the energy figure (0: off)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=128)
@@ -291,14 +293,15 @@ def cpu_oracle_rate(n_sample: int):
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle samples during the timed region."""
+    """nvidia-smi clock, power and throttle samples during a measured region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 200):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
         self.path = None
 
@@ -308,7 +311,8 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms",
+                 str(self.interval_ms)],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -322,27 +326,73 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
+        with open(self.path) as f:
+            lines = f.read().splitlines()
+        os.unlink(self.path)
+        return self.summarize(lines, self.gpu)
+
+    @staticmethod
+    def summarize(lines, gpu: int):
+        """Median SM clock and power, the clock ceiling and the active
+        throttle reasons of one GPU's csv lines; None without samples."""
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                if int(parts[0]) != self.gpu:
+                if int(parts[0]) != gpu:
                     continue
                 sm.append(float(parts[1]))
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        os.unlink(self.path)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+                "reasons": sorted(reasons), "power_w": statistics.median(pw) if pw else None}
+
+
+def measure_energy(step, gpu: int, points_per_step: int, seconds: float = 3.0, idle_seconds: float = 1.0):
+    """Energy per hull, as in the paper's energy study but from the GPU's
+    own power readings (nvidia-smi, NVML) instead of RAPL: the median board
+    power while the GPU idles for idle_seconds, then while the step runs back
+    to back for `seconds`.  Returns the energy per step in total and above
+    idle, and Gpoints per joule."""
+    import torch
+    torch.cuda.synchronize()
+    idle = ClockSampler(gpu, 100)
+    idle.start()
+    time.sleep(idle_seconds)
+    ri = idle.stop()
+    load = ClockSampler(gpu, 100)
+    load.start()
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        step()
+        n += 1
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    rl = load.stop()
+    if not ri or not rl or ri.get("power_w") is None or rl.get("power_w") is None:
+        return {"unavailable": "no power samples from nvidia-smi"}
+    per_step_s = sec / n
+    j_total = rl["power_w"] * per_step_s
+    j_above = (rl["power_w"] - ri["power_w"]) * per_step_s
+    return {"idle_w": ri["power_w"], "load_w": rl["power_w"], "steps": n, "seconds": sec,
+            "joules_per_step": j_total, "joules_per_step_above_idle": j_above,
+            "gpoints_per_joule": points_per_step / j_total / 1e9 if j_total > 0 else None,
+            "load_clocks": {k: rl[k] for k in ("sm_mhz", "sm_max_mhz", "samples", "reasons")},
+            "source": "nvidia-smi power.draw every 100 ms; idle-subtracted figure uses the idle median"}
 
 
 def run_reference(args, ws, rank):
@@ -507,6 +557,14 @@ def main():
                "h2d_bytes_per_step": 2 * 16 * n, "d2h_bytes_per_step": 4 * int(sum(hs)),
                "steps": ksteps, "api": "vq_hull2d_host (pinned host buffers)"}
 
+    # energy per hull (idle-subtracted board power over back-to-back steps)
+    energy = None
+    if ws == 1 and args.energy_seconds > 0:
+        try:
+            energy = measure_energy(step, local, 2 * n, seconds=args.energy_seconds)
+        except Exception as exc:  # the figure is optional; the bench line is not
+            energy = {"unavailable": f"{type(exc).__name__}: {exc}"}
+
     # batched and serving comparisons (one GPU: reported at N = 1)
     batched = serving = None
     if ws == 1 and not args.no_batched:
@@ -530,7 +588,7 @@ def main():
                        "l2": "no flush: each input (1.6 GB at 1e8 points) exceeds L2",
                        "parallelism": f"replicas x{ws}", "hull_sizes": hull_sizes},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "batched": batched, "serving": serving,
+            "batched": batched, "serving": serving, "energy": energy,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "tuning": {"points_per_lane": int(vq.vq_get_config().points_per_thread),
                        "small_max": int(vq.vq_get_config().small_max),

@@ -50,3 +50,23 @@ def test_cpu_batched_baseline_sample():
     k = int(r["sample"].split()[2])
     assert 1 <= k <= 64 and int(offs[k]) <= 100_000 or k == 1
     assert r["hulls_per_s"] > 0 and r["cores"] >= 1 and r["kind"] == "oracle"
+
+
+def test_clock_sampler_summary():
+    """nvidia-smi csv lines (no header, no units) reduce to the median SM
+    clock and power, the ceiling and the active throttle reasons of one GPU;
+    unparsable power readings are skipped, other GPUs' lines ignored."""
+    sys.path.insert(0, ROOT)
+    import bench
+    lines = [
+        "0, 1900, 2070, 700.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2000, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "1, 500, 2070, 100.0, 0x0, Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, [N/A], 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    s = bench.ClockSampler.summarize(lines, 0)
+    assert s["samples"] == 3 and s["sm_mhz"] == 2000 and s["sm_max_mhz"] == 2070
+    assert s["power_w"] == (700.5 + 900.0) / 2
+    assert s["reasons"] == ["sw_power_cap"]
+    assert bench.ClockSampler.summarize(["garbage"], 0) is None
