@@ -133,7 +133,6 @@ __device__ __forceinline__ int classify_a(const SegGeom& g, const LineF& l1, con
   return classify_filter(g, l1, l2, ux, uy, key, err);
 }
 
-
 // Stage one array.  Elements [0, count) of src (element size ES, src
 // ES-aligned) go to slots sh .. sh+count-1 of dst, sh = (src mod 16) / ES.
 // The bulk part is the 16-byte-aligned cover of the range, clipped to the

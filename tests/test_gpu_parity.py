@@ -155,6 +155,28 @@ def test_batched_empty_sets(vq):
         assert np.array_equal(hi[ho[s]:ho[s + 1]], oracle.hull(x[a:b], y[a:b]))
 
 
+def test_batched_mixed_tiers(vq):
+    """Sets inside and outside the FP32 tier's range in one call: the
+    partition kernel compiled with both tiers runs the pre-filter on the
+    sets that have it and the FP64 tier on the others."""
+    parts, dists = [], []
+    for s, (dist, n, scale) in enumerate((("disk", 300_000, 1.0), ("square", 200_000, 2.0 ** 45),
+                                           ("kuzmin", 250_000, 1.0), ("disk", 150_000, 2.0 ** 50),
+                                           ("square", 400_000, 1.0))):
+        x, y = synth.points(dist, n, 300 + s)
+        parts.append((x * scale, y * scale))
+    offs = np.zeros(len(parts) + 1, dtype=np.int64)
+    np.cumsum([p[0].shape[0] for p in parts], out=offs[1:])
+    x = np.concatenate([p[0] for p in parts])
+    y = np.concatenate([p[1] for p in parts])
+    hi, ho = vq.vq_hull2d_batched(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(),
+                                  torch.from_numpy(offs).cuda())
+    hi, ho = hi.cpu().numpy(), ho.cpu().numpy()
+    for s in range(len(parts)):
+        a, b = offs[s], offs[s + 1]
+        assert np.array_equal(hi[ho[s]:ho[s + 1]], oracle.hull(x[a:b], y[a:b])), s
+
+
 def test_host_entry_point(vq):
     x, y = synth.points("kuzmin", 200_000, 3)
     got = vq.vq_hull2d_host(x, y)
