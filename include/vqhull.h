@@ -110,9 +110,11 @@ vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, 
  * allocation from inside a library call -- work recorded while a CUDA graph
  * is being captured, hosts that forbid allocation after start-up, and
  * processes whose device memory is handed out by their own pool allocator.
- * It runs the same kernels as vq_hull2d, but its whole workspace is one
- * fixed 64 MiB array of device memory that is part of this library; every
- * GPU that loads the library reserves it until the process exits.  The call
+ * It runs the same kernels as vq_hull2d (with the host-driven level loop
+ * and without the level-0 pre-filter, which changes no hull), but its whole
+ * workspace is one fixed 64 MiB array of device memory that is part of this
+ * library; every GPU that loads the library reserves it until the process
+ * exits.  The call
  * makes no cudaMalloc, cudaMallocHost, cudaFree or other allocating call.
  *   x, y, hull_idx, h, stream   as for vq_hull2d (hull_idx: room for n)
  *   n                           0 <= n <= 1,048,576; larger n returns
