@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/vqhull.h"
+#include "vq_admit.h"
 #include "vq_internal.h"
 
 namespace {
@@ -108,10 +109,25 @@ struct vq_server {
   vq_server_info info{};
 };
 
+static size_t batch_bytes(long long points, int sets) { return batch_layout(points, sets).total; }
+
+// How many queued requests a lane admits now, FIFO from the head, within
+// the request slots and the memory budget (caller holds mu); limit > 0
+// looks at no more than that many requests.
+static int admit_count(const vq_server* s, int limit, long long* points, size_t* bytes) {
+  int nq = (int)std::min<size_t>(s->queue.size(), (size_t)std::max<long long>(s->cfg.max_inflight - s->resident, 0));
+  if (limit > 0) nq = std::min(nq, limit);
+  std::vector<int64_t> sizes((size_t)nq);
+  for (int i = 0; i < nq; i++) sizes[(size_t)i] = s->queue[(size_t)i]->n;
+  return vq::admit_prefix(sizes.data(), nq, s->resident, s->used, s->cfg.max_inflight, s->cfg.mem_budget_bytes,
+                          batch_bytes, points, bytes);
+}
+
 // The queue's head can be admitted now (caller holds mu).
 static bool admissible(const vq_server* s) {
-  if (s->queue.empty() || s->resident >= s->cfg.max_inflight) return false;
-  return s->used + batch_layout(s->queue.front()->n, 1).total <= s->cfg.mem_budget_bytes;
+  long long pts = 0;
+  size_t bytes = 0;
+  return admit_count(s, 1, &pts, &bytes) > 0;
 }
 
 // Copies in, runs and copies out one batch on the lane's stream.
@@ -184,15 +200,13 @@ static void lane_main(vq_server* s, Lane* L) {
       s->cv_work.wait(g, [&] { return s->stop || admissible(s); });
       if (s->stop) break;
       // FIFO from the head while request slots and memory allow
-      while (!s->queue.empty() && s->resident + (long long)batch.size() < s->cfg.max_inflight) {
-        Request* r = s->queue.front();
-        const BatchLayout B2 = batch_layout(N + r->n, (int)batch.size() + 1);
-        if (s->used + B2.total > s->cfg.mem_budget_bytes) break;
-        batch.push_back(r);
+      size_t bytes = 0;
+      const int k = admit_count(s, 0, &N, &bytes);
+      for (int i = 0; i < k; i++) {
+        batch.push_back(s->queue.front());
         s->queue.pop_front();
-        N += r->n;
-        B = B2;
       }
+      B = batch_layout(N, k);
       if (s->busy > 0) s->info.admitted_while_busy += (long long)batch.size();
       s->busy++;
       s->resident += (long long)batch.size();

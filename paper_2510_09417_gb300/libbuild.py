@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libvqhull.so")
 STAMP = os.path.join(BUILD, "lib.arch")
 SOURCES = ["vq_kernels.cu", "vq_api.cu", "vq_server.cu", "vq_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, h) for h in ("vq_device.cuh", "vq_internal.h", "vq_partition.cuh")] + [
+HEADERS = [os.path.join(CSRC, h) for h in ("vq_device.cuh", "vq_internal.h", "vq_partition.cuh", "vq_admit.h")] + [
     os.path.join(ROOT, "include", "vqhull.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

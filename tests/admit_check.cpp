@@ -1,0 +1,27 @@
+// Host-only check of the serving handle's admission policy (vq_admit.h):
+// prints one line per case, "name k points bytes"; the test compares them
+// with the expected values.
+#include <cstdio>
+
+#include "vq_admit.h"
+
+static size_t model_bytes(long long points, int sets) { return (size_t)(68 * points + 1000 * sets); }
+
+static void run(const char* name, const int64_t* sizes, int nq, long long resident, size_t used, long long slots,
+                size_t budget) {
+  long long pts = -1;
+  size_t bytes = 0;
+  const int k = vq::admit_prefix(sizes, nq, resident, used, slots, budget, model_bytes, &pts, &bytes);
+  std::printf("%s %d %lld %zu\n", name, k, pts, bytes);
+}
+
+int main() {
+  const int64_t q[4] = {100, 200, 300, 400};
+  run("all", q, 4, 0, 0, 64, 1u << 30);               // everything fits
+  run("slots", q, 4, 1, 0, 3, 1u << 30);              // two slots left
+  run("no_slot", q, 4, 3, 0, 3, 1u << 30);            // none left
+  run("budget", q, 4, 0, 0, 64, 68 * 300 + 2000);     // the first two fit exactly
+  run("head_too_big", q, 4, 0, 100000, 64, 100500);   // memory in use leaves too little
+  run("empty", q, 0, 0, 0, 64, 1u << 30);
+  return 0;
+}

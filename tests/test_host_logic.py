@@ -164,3 +164,28 @@ def test_strictly_right_of_every_edge_means_strictly_inside():
             found += 1
             assert hull_strict_inside(poly, u), (poly, u)
     assert found > 50
+
+
+def test_server_admission_policy(tmp_path):
+    """The serving handle's admission (vq_admit.h, host code): the longest
+    FIFO prefix within the free request slots and the memory budget,
+    nothing when the head does not fit.  Compiled with the host compiler."""
+    import os
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        import pytest
+        pytest.skip("no host C++ compiler")
+    exe = tmp_path / "admit_check"
+    subprocess.check_call([cxx, "-std=c++17", "-O1", "-I", os.path.join(root, "paper_2510_09417_gb300", "csrc"),
+                           os.path.join(root, "tests", "admit_check.cpp"), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {l.split()[0]: tuple(int(v) for v in l.split()[1:]) for l in out if l.strip()}
+    assert got["all"] == (4, 1000, 68 * 1000 + 4000)
+    assert got["slots"] == (2, 300, 68 * 300 + 2000)
+    assert got["no_slot"] == (0, 0, 0)
+    assert got["budget"] == (2, 300, 68 * 300 + 2000)
+    assert got["head_too_big"] == (0, 0, 0)
+    assert got["empty"] == (0, 0, 0)
