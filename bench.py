@@ -79,7 +79,35 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=128)
+    ap.add_argument("--profile-one", default="", choices=[""] + list(synth.DISTRIBUTIONS),
+                    help="profiling aid: run --profile-reps hulls of --n points of this distribution "
+                         "(the workload's seed), print their counters and exit")
+    ap.add_argument("--profile-reps", type=int, default=3)
     return ap.parse_args()
+
+
+SEEDS = {"square": 1, "disk": 2, "circle": 3, "kuzmin": 4}
+
+
+def profile_one(args):
+    """The same hull --profile-reps times on cuda:0 (for ncu: the kernels of
+    exactly these hulls run, nothing else), then one line of counters."""
+    import torch
+    import paper_2510_09417_gb300 as vq
+    vq.load()
+    x, y = synth.points(args.profile_one, args.n, SEEDS.get(args.profile_one, 1))
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    del x, y
+    vq.vq_profile_read(reset=True)
+    h = None
+    for _ in range(max(1, args.profile_reps)):
+        h = vq.vq_hull2d(xd, yd)
+    torch.cuda.synchronize()
+    p = vq.vq_profile_read(reset=True)
+    st = vq.vq_last_stats()
+    print(json.dumps({"profile_one": args.profile_one, "n": args.n, "reps": args.profile_reps, "h": int(h.shape[0]),
+                      "launches": p["launches"], "k1_points_read": p["k1_points_read"],
+                      "level_reads": st["read"][:8]}))
 
 
 WORKERS = max(1, min(16, os.cpu_count() or 1))
@@ -432,6 +460,8 @@ def run_reference(args, ws, rank):
 
 def main():
     args = parse()
+    if args.profile_one:
+        return profile_one(args)
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)

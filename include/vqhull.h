@@ -185,13 +185,15 @@ typedef struct {
   int64_t levels;            /* partition levels run by the level loop        */
   int64_t k1_points_read;    /* points classified by the partition kernel     */
   int64_t k1_points_kept;    /* of those, points written to a child           */
-  double k0_ms;              /* extreme-point pass                            */
+  double k0_ms;              /* extreme-point pass (with the pre-filter: the
+                                sieve and the per-set finalize)              */
   double k1_ms;              /* partition kernel                              */
   double k2_ms;              /* per-segment finalize                          */
   double k3_ms;              /* small-segment finisher                        */
   double k4_ms;              /* ordering                                      */
   double other_ms;           /* scans, tile maps, counter resets              */
   int64_t graph_launches;    /* level loops run as a device-driven graph      */
+  double sample_ms;          /* pre-filter set-up: sampled extremes and chains */
 } vq_profile;
 
 vq_status vq_profile_read(vq_profile* out, int32_t reset);

@@ -7,6 +7,7 @@
 // clockwise order (k_k4_*).
 #include <climits>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <mutex>
@@ -43,10 +44,22 @@ static vq_status cuda_status(cudaError_t e) {
   return VQ_ERR_CUDA;
 }
 
-#define VQ_CHECK(call)                                  \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return cuda_status(e_);      \
+// VQ_DEBUG=1 in the environment prints the failing runtime call
+static bool debug_on() {
+  static const int on = [] {
+    const char* v = getenv("VQ_DEBUG");
+    return v && v[0] == '1' ? 1 : 0;
+  }();
+  return on != 0;
+}
+
+#define VQ_CHECK(call)                                                                                  \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) {                                                                            \
+      if (debug_on()) fprintf(stderr, "vqhull: %s:%d %s: %s\n", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return cuda_status(e_);                                                                           \
+    }                                                                                                   \
   } while (0)
 
 // A captured device-driven level loop: one CUDA graph whose WHILE node
@@ -64,7 +77,7 @@ constexpr int kGraphCache = 16;           // graphs kept per device (least recen
 // round trips, so smaller runs keep the host loop unless their graph is
 // already cached.
 constexpr long long kGraphMinPoints = 1ll << 22;
-constexpr int kGraphKernelsPerIter = 11;  // two levels of 5 kernels, and the condition
+constexpr int kGraphKernelsPerIter = 13;  // two levels of 6 kernels (two partition tiers), and the condition
 
 struct Ctx {
   std::mutex mu;
@@ -102,7 +115,7 @@ struct Ctx {
   unsigned long long graph_clock = 0;
 };
 
-enum { kKindOther = 0, kKindK0, kKindK1, kKindK2, kKindK3, kKindK4 };
+enum { kKindOther = 0, kKindK0, kKindK1, kKindK2, kKindK3, kKindK4, kKindSample };
 
 // Brackets kernel launches with CUDA events on the call's stream when
 // profiling is on; the times are summed per kernel kind after the call.
@@ -146,6 +159,7 @@ struct Timer {
         case kKindK2: c.prof.k2_ms += ms; break;
         case kKindK3: c.prof.k3_ms += ms; break;
         case kKindK4: c.prof.k4_ms += ms; break;
+        case kKindSample: c.prof.sample_ms += ms; break;
         default: c.prof.other_ms += ms; break;
       }
     }
@@ -185,10 +199,14 @@ static size_t layout(Work& w, char* base, long long N, int nsets, long long nkey
   w.slot = reinterpret_cast<int*>(take(sizeof(int) * (nkeys + 1)));
   w.bitmap = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * ((nkeys + 31) / 32 + 1)));
   w.sets = reinterpret_cast<SetRec*>(take(sizeof(SetRec) * nsets));
-  w.oct = reinterpret_cast<OctF*>(take(sizeof(OctF) * nsets));
+  w.sieve = cfg.prefilter ? 1 : 0;
+  w.poly = reinterpret_cast<PolyF*>(take(w.sieve ? sizeof(PolyF) * nsets : 0));
+  w.dirbest = reinterpret_cast<unsigned long long*>(take(w.sieve ? sizeof(unsigned long long) * kPolyDirs * nsets : 0));
+  w.nsurv = reinterpret_cast<int*>(take(w.sieve ? sizeof(int) * nsets : 0));
   w.k0_tile_start = reinterpret_cast<int*>(take(sizeof(int) * (nsets + 1)));
   w.capT0 = (int)(n / kK0Tile + nsets + 1);
-  w.k0part = reinterpret_cast<K0Part*>(take(sizeof(K0Part) * w.capT0));
+  // partials: one per extreme-pass tile, or (sieve) one per block and set
+  w.k0part = reinterpret_cast<K0Part*>(take(sizeof(K0Part) * (w.sieve ? (size_t)kSvMaxBlocks + nsets : (size_t)w.capT0)));
   w.small_max = cfg.small_max;
   // partition tile: one warp's (32 x ppt points), or one look-back block's
   w.tile = (cfg.ordered ? kK1Threads : kWarp) * cfg.ppt;
@@ -289,15 +307,19 @@ static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cach
   LevelGraph g;
   g.key = key;
   VQ_CHECK(cudaGraphCreate(&g.graph, 0));
+  // the loop's condition starts at 0 on every launch; a kernel node ahead
+  // of the WHILE node sets it from level 0's result, and the body's last
+  // kernel sets it for the next iteration
   cudaGraphConditionalHandle h;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g.graph, 1, cudaGraphCondAssignDefault);
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g.graph, 0, cudaGraphCondAssignDefault);
   cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};  // the rest zero
-  cudaGraphNode_t node;
+  cudaGraphNode_t init_node, node;
+  if (e == cudaSuccess) e = add_loop_init_node(g.graph, &init_node, w, h);
   if (e == cudaSuccess) {
     p.conditional.handle = h;
     p.conditional.type = cudaGraphCondTypeWhile;
     p.conditional.size = 1;
-    e = cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &p);
+    e = cudaGraphAddNode(&node, g.graph, &init_node, nullptr, 1, &p);
   }
   if (e == cudaSuccess) {
     cudaGraph_t body = p.conditional.phGraph_out[0];
@@ -367,7 +389,6 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   w.timeout_ns = cfg.timeout_ns;
   w.drop_tile = cfg.drop_tile;
   w.ordered = cfg.ordered;
-  w.prefilter = cfg.prefilter;
   c.d_stats = w.stats;
 
   const long long launches0 = kernels_launched();
@@ -379,15 +400,26 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   VQ_CHECK(launch_seed(w, st));
   VQ_CHECK(scan_exclusive_i32(w.k0_tile_start, (long long)nsets + 1, reinterpret_cast<int*>(scan_tmp), st));
   VQ_CHECK(tm.end());
+  if (w.sieve) {
+    VQ_CHECK(cudaMemsetAsync(w.dirbest, 0, sizeof(unsigned long long) * kPolyDirs * nsets, st));
+    VQ_CHECK(cudaMemsetAsync(w.nsurv, 0, sizeof(int) * nsets, st));
+  }
+  VQ_CHECK(tm.end());
+  if (w.sieve) {  // pre-filter path: sample, chains, sieve (the extreme pass over the kept points)
+    VQ_CHECK(tm.begin(kKindSample));
+    VQ_CHECK(launch_sample(w, st));
+    VQ_CHECK(launch_poly(w, st));
+    VQ_CHECK(tm.end());
+  }
   VQ_CHECK(tm.begin(kKindK0));
-  VQ_CHECK(launch_k0(w, c.sms * 2, st));  // resident blocks only (2 per SM); tiles of kK0Tile points
+  if (w.sieve) {
+    VQ_CHECK(launch_sieve(w, st));
+  } else {
+    VQ_CHECK(launch_k0(w, c.sms * 2, st));  // resident blocks only (2 per SM); tiles of kK0Tile points
+  }
   VQ_CHECK(launch_k0_finalize(w, st));
   VQ_CHECK(tm.end());
   VQ_TIMED(tm, kKindOther, launch_tilemap(w, 0, c.sms * 4, st));
-  // which partition kernel: FP32-only unless some set needs the FP64 tier
-  VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-  VQ_CHECK(cudaStreamSynchronize(st));
-  w.all_fast = c.h_ctrl->any_slow ? 0 : 1;
 
   int level = 0;
   int levels_run = 0;
@@ -396,39 +428,54 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   // look-back (whose grid is one block per tile)
   const bool device_loop = !cfg.host_loop && !cfg.profile && !cfg.ordered;
   bool graph_ran = false;
-  // one partition block per tile: level 0 uses the bound (one segment per
-  // point set), later levels the count the previous level produced
-  long long k1_grid = N / w.tile + nsets + 1;
-  for (;; level++) {
-    VQ_TIMED(tm, kKindOther, launch_prologue(w, level, st));
-    if (k1_grid > 0) VQ_TIMED(tm, kKindK1, launch_k1(w, level, cfg.ppt, (int)k1_grid, st));
+  cudaGraphExec_t ex = nullptr;
+  if (device_loop && !c.graph_off) {
+    // the partition kernel's tier is picked on the device, so the call has
+    // no host round trip before its end
+    w.tier_dev = 1;
+    if (level_graph(c, w, cfg, N < kGraphMinPoints, &ex) != VQ_OK) {
+      c.graph_off = true;  // nothing was launched: the host loop runs instead
+      ex = nullptr;
+      fprintf(stderr, "vqhull: the device-driven level loop could not be built; using the host loop\n");
+    }
+    if (!ex) w.tier_dev = 0;
+  }
+  if (ex) {
+    // level 0 from the host, then every later level inside one graph launch
+    VQ_CHECK(launch_prologue(w, 0, st));
+    VQ_CHECK(launch_k1(w, 0, cfg.ppt, (int)(N / w.tile + nsets + 1), st));
     c.prof.k1_launches++;
-    VQ_TIMED(tm, kKindK2, launch_k2(w, level, c.sms * 8, st));
-    VQ_TIMED(tm, kKindOther, launch_tilemap(w, (level + 1) & 1, c.sms * 4, st));
-    VQ_TIMED(tm, kKindK3, launch_k3(w, c.sms * 2, st));
+    VQ_CHECK(launch_k2(w, 0, c.sms * 8, st));
+    VQ_CHECK(launch_tilemap(w, 1, c.sms * 4, st));
+    VQ_CHECK(launch_k3(w, c.sms * 2, st));
+    VQ_CHECK(cudaGraphLaunch(ex, st));
+    graph_ran = true;
+    levels_run = 1;
+  } else {
+    // which partition kernel: FP32-only unless some set needs the FP64 tier
     VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     VQ_CHECK(cudaStreamSynchronize(st));
-    levels_run = level + 1;
-    if (c.h_ctrl->err & kErrFatal) break;
-    if (c.h_ctrl->k1_segs[(level + 1) & 1] == 0) break;
-    if (device_loop && level == 0 && !c.graph_off) {
-      cudaGraphExec_t ex = nullptr;
-      if (level_graph(c, w, cfg, N < kGraphMinPoints, &ex) != VQ_OK) {
-        // nothing was launched: the levels run from the host loop instead
-        c.graph_off = true;
-        ex = nullptr;
-        fprintf(stderr, "vqhull: the device-driven level loop could not be built; using the host loop\n");
-      }
-      if (ex) {
-        VQ_CHECK(cudaGraphLaunch(ex, st));
-        graph_ran = true;
+    w.all_fast = c.h_ctrl->any_slow ? 0 : 1;
+    // one partition block per tile: level 0 uses the bound (one segment per
+    // point set), later levels the count the previous level produced
+    long long k1_grid = N / w.tile + nsets + 1;
+    for (;; level++) {
+      VQ_TIMED(tm, kKindOther, launch_prologue(w, level, st));
+      if (k1_grid > 0) VQ_TIMED(tm, kKindK1, launch_k1(w, level, cfg.ppt, (int)k1_grid, st));
+      c.prof.k1_launches++;
+      VQ_TIMED(tm, kKindK2, launch_k2(w, level, c.sms * 8, st));
+      VQ_TIMED(tm, kKindOther, launch_tilemap(w, (level + 1) & 1, c.sms * 4, st));
+      VQ_TIMED(tm, kKindK3, launch_k3(w, c.sms * 2, st));
+      VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      VQ_CHECK(cudaStreamSynchronize(st));
+      levels_run = level + 1;
+      if (c.h_ctrl->err & kErrFatal) break;
+      if (c.h_ctrl->k1_segs[(level + 1) & 1] == 0) break;
+      k1_grid = c.h_ctrl->k1_tiles[(level + 1) & 1];
+      if (level > N + 1) {  // every level removes at least one point per segment
+        c.h_ctrl->err |= kErrInternal;
         break;
       }
-    }
-    k1_grid = c.h_ctrl->k1_tiles[(level + 1) & 1];
-    if (level > N + 1) {  // every level removes at least one point per segment
-      c.h_ctrl->err |= kErrInternal;
-      break;
     }
   }
   c.last_levels = levels_run;
@@ -439,7 +486,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   if (graph_ran) {
     const long long iters = c.h_ctrl->graph_iters;
     levels_run = 1 + c.h_ctrl->live_levels;
-    count_launches(iters * kGraphKernelsPerIter);
+    count_launches(1 + iters * kGraphKernelsPerIter);  // the loop's first test, then the body
     c.prof.k1_launches += 2 * iters;
     c.prof.graph_launches++;
   }

@@ -38,7 +38,6 @@ constexpr unsigned kErrFatal = kErrTimeout | kErrCapacity | kErrInternal | kErrB
 constexpr int kSegFast = 1;       // FP32 tier allowed (all |coords| < 2^40)
 constexpr int kSegSrcInput = 2;   // points still in the caller's arrays (level 0)
 constexpr int kSegSrcBuf1 = 4;    // points in ping-pong buffer 1 (else buffer 0)
-constexpr int kSegOct = 8;        // level 0: the set's pre-filter chains apply (Work::oct[segment])
 
 // look-back status words: 2 flag bits, 31-bit left count, 31-bit right count
 constexpr unsigned long long kStAgg = 1ull << 62;
@@ -68,7 +67,7 @@ struct Ctrl {
   int dbg_site;             // checked builds: first failed bounds check
   int fill_jobs[2];         // tile-map fill jobs per level parity
   int any_slow;             // some point set needs the FP64 tier (|coordinate| >= 2^40)
-  int pad0;
+  int sv_grid;              // blocks of the last sieve launch (its partials are per block and set)
   long long k1_nw[2];       // warps of the last partition launch per level parity
   long long dbg_val;        // checked builds: the offending value
   unsigned long long k1prof[12];  // profiling builds: partition-kernel cycle and event counters
@@ -177,8 +176,6 @@ struct K0Part {
   int mini, maxi;
   int flags;  // bit0 nonfinite, bit1 out of FP32 range
   int pad;
-  float ov[6];  // pre-filter directions (see K0Dir), approximate scores
-  int oi[6];    // and the points that reach them
 };
 
 // ---------------------------------------------------------------------------
@@ -520,62 +517,97 @@ __device__ __forceinline__ LineF line2_of(const SegGeom& g) {
 }
 
 // ---------------------------------------------------------------------------
-// Level-0 pre-filter: the Akl-Toussaint octagon that the paper proposes as
-// its next step (Sec. 6, with the figure of p1..p8).  Per point set, an
-// upper chain p = v0, v1, .., vk = q of input points (x strictly
-// increasing, every inner vertex strictly left of p->q, strict right turns)
-// and a lower chain q, .., p likewise.  The polygon p, upper chain, q is
-// convex and its vertices are input points, so a point strictly inside it
-// is strictly inside the hull: it is never a strict vertex nor a farthest
-// point of any segment, and level 0 drops it before classifying it.  The
-// test (oct_inside) uses the FP32 tier with its bound; every uncertain case
-// keeps the point.
+// Level-0 pre-filter: the Akl-Toussaint heuristic that the paper proposes as
+// its next step (Sec. 6, the octagon p1..p8 from the extremes of x, y, x - y
+// and x + y), here with kPolyDirs sampled directions instead of eight.
+// Per point set, two x-monotone chains of input points run from the
+// leftmost candidate L to the rightmost R: the upper chain (thresholds tu,
+// edges eu) and the lower chain (tl, el), vertices in strictly increasing x.
+// Let Q be the open region strictly below the upper chain and strictly
+// above the lower chain over L.x < x < R.x.  Every point of Q lies on an
+// open vertical segment between two points of the chains, so Q lies in the
+// convex hull of the chains' vertices, and Q is open, so it lies in the
+// interior of that hull: a point of Q is strictly inside the hull of its
+// set.  Such a point is neither a strict vertex nor the farthest point of
+// any segment (farthest points maximise a linear function over the set, so
+// they lie on a supporting line of the hull), and dropping it leaves every
+// result of Alg. 1 unchanged.  None of this needs the chains to be convex,
+// so they are built with approximate arithmetic; only the per-point test
+// must be certain: FP32 tier with its bound, and equal thresholds or
+// inconclusive signs keep the point.
+// An axis-parallel box whose four corners passed that same certain test
+// lies in the convex hull of the corners, hence in the set's hull, and a
+// point strictly inside the box is strictly inside the hull.  The box test
+// compares the coordinates' high words read as FP32 numbers (hword): no
+// arithmetic at all.
 // ---------------------------------------------------------------------------
 
-struct OctSide {
-  float t[3];   // sx * trunc_f32(x) of the inner vertices in chain order, +inf past the last
-  float sx;     // +1 for the upper chain (x increasing), -1 for the lower chain
-  LineF e[4];   // edge j runs from vertex j to vertex j + 1
-};
-struct OctF {
-  OctSide s[2];  // [0]: upper chain (points left of p->q), [1]: lower chain
-  // An axis-parallel box whose closed extent lies in the closed polygon
-  // (checked exactly), as truncated bounds: trunc_f32(x) > bx0 implies
-  // x > the exact bound, so a point passing the four strict tests is
-  // strictly inside the polygon.  Empty (bx0 = +inf) when none was found.
-  float bx0, bx1, by0, by1;
+constexpr int kPolyDirs = 32;    // sampled directions (integer pairs, see k_sample)
+constexpr int kChainEdges = 16;  // at most 16 edges (15 inner vertices) per chain
+
+constexpr int kPolyBoxes = 3;    // inner boxes per set (aspect ratios 1, wide, tall)
+
+struct alignas(16) PolyF {
+  float box[kPolyBoxes][4];  // inner boxes: hword of x0, x1, y0, y1; empty: x0 = +inf
+  float xl, xr;              // trunc_f32 of L.x and R.x
+  int on;                    // 1: the chains apply
+  int pad;
+  float tu[kChainEdges];     // trunc_f32(x) of the upper chain's inner vertices, increasing; +inf padded
+  float tl[kChainEdges];     // the same for the lower chain
+  float4 eu[kChainEdges][2];  // upper edge j (vertex j -> j + 1): {ox, oy, dx, dy}, {k, c, 0, 0}
+  float4 el[kChainEdges][2];  // lower edges, likewise (left to right)
 };
 
-// The edge of chain S above (upper) or below (lower) abscissa x, from the
-// truncated x (fx): j with x certainly between the x of vertices j and
-// j + 1 (trunc_f32 is monotone, so fx > t ensures x >= the vertex's x).
-// -1 when fx equals a threshold (x undecided against that vertex).
-__device__ __forceinline__ int oct_edge(const OctSide& S, float fx) {
-  const float v = S.sx * fx;
-  if (v == S.t[0] || v == S.t[1] || v == S.t[2]) return -1;
-  return (v > S.t[0] ? 1 : 0) + (v > S.t[1] ? 1 : 0) + (v > S.t[2] ? 1 : 0);
+// The high word of a double read as an FP32 number.  For doubles u, v:
+// hword(u) > hword(v) implies u > v.  Both positive: the high word is a
+// prefix of the bit pattern, whose order is the value order.  Both
+// negative: likewise with the order reversed, as for FP32.  Mixed signs and
+// zeros: -0 and +0 compare equal in FP32, and a nonzero high word has a
+// nonzero value.  A double of magnitude 2^1017 or more reads as an
+// infinity (the implication still holds) or a NaN (every compare fails).
+__device__ __forceinline__ float hword(double v) { return __int_as_float(__double2hiint(v)); }
+
+// The point is certainly strictly inside one of the inner boxes.
+__device__ __forceinline__ bool in_boxes(const float (&b)[kPolyBoxes][4], float hx, float hy) {
+  bool in = false;
+#pragma unroll
+  for (int k = 0; k < kPolyBoxes; k++) in = in || (hx > b[k][0] && hx < b[k][1] && hy > b[k][2] && hy < b[k][3]);
+  return in;
 }
 
-// The point is certainly strictly inside the inner box (four compares).
-__device__ __forceinline__ bool oct_in_box(const OctF& O, double ux, double uy) {
-  const float fx = trunc_f32(ux), fy = trunc_f32(uy);
-  return fx > O.bx0 && fx < O.bx1 && fy > O.by0 && fy < O.by1;
+// Edge of a chain over the truncated abscissa v: the number of inner
+// thresholds below v (binary search over 16 entries, the last one +inf),
+// or -1 when v equals a threshold (x undecided against that vertex).  For
+// a result j, trunc_f32's monotonicity gives x(vertex j) < x < x(vertex
+// j + 1) for the inner vertices involved.
+__device__ __forceinline__ int chain_edge(const float* t, float v) {
+  int j = 0;
+#pragma unroll
+  for (int s = kChainEdges / 2; s >= 1; s >>= 1) j += t[j + s - 1] < v ? s : 0;
+  return t[j] == v ? -1 : j;
 }
 
-// The point is certainly strictly inside the polygon p, upper chain, q,
-// lower chain: certainly right of the upper chain's edge over its x and of
-// the lower chain's edge under it.  The polygon is convex (both chains are,
-// and p and q are the extremes in x), so its vertical section at x is the
-// segment between those two edges.
-__device__ __forceinline__ bool oct_inside(const OctF& O, double ux, double uy) {
+__device__ __forceinline__ LineF poly_edge(const float4 (*e)[2], int j) {
+  const float4 a = e[j][0], b = e[j][1];
+  LineF L;
+  L.ox = a.x; L.oy = a.y; L.dx = a.z; L.dy = a.w; L.k = b.x; L.c = b.y;
+  return L;
+}
+
+// The point is certainly in the region Q of the chains (see above).
+__device__ __forceinline__ bool poly_inside(const PolyF& P, double ux, double uy) {
+  const unsigned ax = static_cast<unsigned>(__double2hiint(ux)) & 0x7fffffffu;
+  const unsigned ay = static_cast<unsigned>(__double2hiint(uy)) & 0x7fffffffu;
+  if (max(ax, ay) >= 0x42700000u) return false;  // |coordinate| >= 2^40 or non-finite: outside the FP32 tier
   const float fx = trunc_f32(ux), fy = trunc_f32(uy);
-  const int ju = oct_edge(O.s[0], fx), jl = oct_edge(O.s[1], fx);
-  if (ju < 0 || jl < 0) return false;
+  if (!(fx > P.xl && fx < P.xr)) return false;
+  const int ju = chain_edge(P.tu, fx), jl = chain_edge(P.tl, fx);
+  if ((ju | jl) < 0) return false;
   const float m = __fadd_ru(fabsf(fx), fabsf(fy));
   float du, eu, dl, el;
-  orient_f32(O.s[0].e[ju], fx, fy, m, du, eu);
-  orient_f32(O.s[1].e[jl], fx, fy, m, dl, el);
-  return du < -eu && dl < -el;
+  orient_f32(poly_edge(P.eu, ju), fx, fy, m, du, eu);
+  orient_f32(poly_edge(P.el, jl), fx, fy, m, dl, el);
+  return du < -eu && dl > el;  // certainly below the upper edge and above the lower edge
 }
 
 // ---------------------------------------------------------------------------

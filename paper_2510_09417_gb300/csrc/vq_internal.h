@@ -14,7 +14,10 @@ constexpr int kK0Threads = 256;
 constexpr int kK0Tile = 32768;      // points per extreme-pass tile
 constexpr int kK0Pairs = 2;         // extreme pass: point pairs per array, thread and stage
 constexpr int kK0Stages = 4;        // extreme pass: shared-memory ring stages (64 KB per block)
-constexpr int kK0OctEvery = 8;      // extreme pass: pre-filter candidates from every 8th tile of a set (power of 2)
+constexpr int kSampleChunk = 4096;  // pre-filter sample: the first kSampleChunk points of every
+constexpr int kSampleEvery = 16;    // kSampleEvery-th extreme-pass tile of a set (1/128 of the points)
+constexpr int kSvWarps = 8;         // sieve: warps per block
+constexpr int kSvMaxBlocks = 4096;  // sieve: most blocks (its partials: one per block and set)
 constexpr int kK3Cap = 1024;        // points per warp in the small-segment kernel
 constexpr int kK3Warps = 4;
 constexpr int kK3Stack = 24;
@@ -58,17 +61,28 @@ struct Work {
   int drop_tile;             // test knob: this K1 tile never publishes (-1: none)
   int ordered;               // 1: offsets by decoupled look-back (stable layout); 0: atomic cursors
   int all_fast;              // host's copy of !Ctrl::any_slow: selects the FP32-only partition kernel
-  OctF* oct;                 // per level-0 segment (slot < nsets): pre-filter chains, or null (no pre-filter)
-  int prefilter;             // 1: level 0 drops the points inside the pre-filter chains
+  int tier_dev;              // 1: both partition kernels are launched and the device's Ctrl::any_slow
+                             // picks the one that runs (no host round trip); all_fast is then unused
+  PolyF* poly;               // per set: pre-filter chains and inner box
+  unsigned long long* dirbest;  // per set and sampled direction: packed (score, index) of the extreme
+  int* nsurv;                // per set: points the sieve kept (written to buffer 1 from the set's offset)
+  int sieve;                 // 1: the pre-filter path (sample, chains, sieve); level 0 reads buffer 1
 };
 
 // launchers (vq_kernels.cu); all enqueue on `st`
 cudaError_t launch_seed(const Work& w, cudaStream_t st);
 cudaError_t launch_k0(const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st);
+// pre-filter path: sampled direction extremes, chains per set, the sieve
+cudaError_t launch_sample(const Work& w, cudaStream_t st);
+cudaError_t launch_poly(const Work& w, cudaStream_t st);
+cudaError_t launch_sieve(const Work& w, cudaStream_t st);
 cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st);
 // condition kernel of the device-driven level loop (a graph WHILE node)
 cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, long long max_iters, cudaStream_t st);
+// a kernel node of graph g (no dependencies) that sets h to whether the
+// level after level 0 has segments (the WHILE node's first test)
+cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphNode_t* node, const Work& w, cudaGraphConditionalHandle h);
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st);
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st);
 cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st);

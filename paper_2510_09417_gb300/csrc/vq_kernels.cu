@@ -234,54 +234,6 @@ __device__ __forceinline__ int k0_flags(unsigned am) {
   return (am >= 0x7ff00000u ? 1 : 0) | (am >= 0x42700000u ? 2 : 0);
 }
 
-// Candidates of the level-0 pre-filter: the points that maximise six
-// scores of the FP32-truncated coordinates: y - x, y, x + y (upper chain,
-// in chain order), x - y, -y, -x - y (lower chain).  The scores are
-// approximate, and only a sample of the points is scored (every eighth
-// tile of a set, and always its first); the chains built from these
-// points are checked exactly, so any choice of points is safe, and a
-// sample of millions of points lands within a hair of the true extremes.
-// Ties go to the lowest index.
-struct K0Oct {
-  float v[6];
-  int i[6];
-};
-__device__ __forceinline__ void oct_init(K0Oct& o) {
-#pragma unroll
-  for (int k = 0; k < 6; k++) {
-    o.v[k] = -INFINITY;
-    o.i[k] = INT_MAX;
-  }
-}
-__device__ __forceinline__ void oct_merge(K0Oct& o, int k, float v, int i) {
-  if (v > o.v[k] || (v == o.v[k] && i < o.i[k])) {
-    o.v[k] = v;
-    o.i[k] = i;
-  }
-}
-// points arrive in increasing index order per thread: a strict > keeps the lowest
-__device__ __forceinline__ void oct_take(K0Oct& o, double vx, double vy, int i) {
-  const float fx = trunc_f32(vx), fy = trunc_f32(vy);
-  const float d = __fsub_rn(fy, fx), s = __fadd_rn(fx, fy);
-  const float sc[6] = {d, fy, s, -d, -fy, -s};
-#pragma unroll
-  for (int k = 0; k < 6; k++)
-    if (sc[k] > o.v[k]) {
-      o.v[k] = sc[k];
-      o.i[k] = i;
-    }
-}
-__device__ __forceinline__ void oct_warp_reduce(K0Oct& o) {
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1)
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-      const float v = __shfl_xor_sync(kFull, o.v[k], m);
-      const int i = __shfl_xor_sync(kFull, o.i[k], m);
-      oct_merge(o, k, v, i);
-    }
-}
-
 // Asynchronous 16-byte global -> shared copies (cp.async, completion
 // tracked per thread by commit groups).
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -294,11 +246,8 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// One tile's points through the shared-memory ring (see k_k0); OCT: the
-// tile is sampled for the pre-filter candidates.
-template <bool OCT>
-__device__ __forceinline__ void k0_stream(const Work& w, int begin, int count, LexPt& mn, LexPt& mx, unsigned& am,
-                                          K0Oct& oc) {
+// One tile's points through the shared-memory ring (see k_k0).
+__device__ __forceinline__ void k0_stream(const Work& w, int begin, int count, LexPt& mn, LexPt& mx, unsigned& am) {
   extern __shared__ __align__(16) double2 k0_ring[];  // [stage][x|y][pair k][thread]
   constexpr int SP = kK0Pairs * kK0Threads;           // pairs per stage
   // pair q covers points 2q, 2q+1; stage i holds pairs i*SP .. i*SP+SP-1
@@ -338,10 +287,6 @@ __device__ __forceinline__ void k0_stream(const Work& w, int begin, int count, L
         const double2 vx = *slot(st, 0, k), vy = *slot(st, 1, k);
         k0_take(vx.x, vy.x, begin + 2 * q, mn, mx, am);
         k0_take(vx.y, vy.y, begin + 2 * q + 1, mn, mx, am);
-        if (OCT) {
-          oct_take(oc, vx.x, vy.x, begin + 2 * q);
-          oct_take(oc, vx.y, vy.y, begin + 2 * q + 1);
-        }
       }
     }
   }
@@ -349,7 +294,6 @@ __device__ __forceinline__ void k0_stream(const Work& w, int begin, int count, L
   if ((count & 1) && threadIdx.x == 0) {
     const int l = begin + count - 1;
     k0_take(w.x[l], w.y[l], l, mn, mx, am);
-    if (OCT) oct_take(oc, w.x[l], w.y[l], l);
   }
 }
 
@@ -364,7 +308,6 @@ __device__ __forceinline__ void k0_stream(const Work& w, int begin, int count, L
 __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
   __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
   __shared__ int s_fl[kK0Threads / kWarp];
-  __shared__ K0Oct s_oc[kK0Threads / kWarp];
   const int total = w.k0_tile_start[w.nsets];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -379,21 +322,12 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
     const int count = min(kK0Tile, S.len - j * kK0Tile);
     LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
     unsigned am = 0;
-    K0Oct oc;
-    oct_init(oc);
     const bool vec = ((reinterpret_cast<uintptr_t>(w.x + begin) | reinterpret_cast<uintptr_t>(w.y + begin)) & 15u) == 0;
-    // pre-filter candidates from every kK0OctEvery-th tile of a set (its
-    // first tile always)
-    const bool sample = (j & (kK0OctEvery - 1)) == 0;
     if (vec) {
-      if (sample) k0_stream<true>(w, begin, count, mn, mx, am, oc);
-      else k0_stream<false>(w, begin, count, mn, mx, am, oc);
+      k0_stream(w, begin, count, mn, mx, am);
     } else {
 #pragma unroll 8
-      for (int l = threadIdx.x; l < count; l += kK0Threads) {
-        k0_take(w.x[begin + l], w.y[begin + l], begin + l, mn, mx, am);
-        if (sample) oct_take(oc, w.x[begin + l], w.y[begin + l], begin + l);
-      }
+      for (int l = threadIdx.x; l < count; l += kK0Threads) k0_take(w.x[begin + l], w.y[begin + l], begin + l, mn, mx, am);
     }
     int fl = k0_flags(am);
 #pragma unroll
@@ -403,27 +337,19 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
       if (lex_max_better(b, mx)) mx = b;
       fl |= __shfl_xor_sync(kFull, fl, m);
     }
-    oct_warp_reduce(oc);
-    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; s_oc[warp] = oc; }
+    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; }
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int q = 1; q < kK0Threads / kWarp; q++) {
         if (lex_min_better(s_mn[q], mn)) mn = s_mn[q];
         if (lex_max_better(s_mx[q], mx)) mx = s_mx[q];
         fl |= s_fl[q];
-#pragma unroll
-        for (int k = 0; k < 6; k++) oct_merge(oc, k, s_oc[q].v[k], s_oc[q].i[k]);
       }
       K0Part P;
       P.minx = mn.kx; P.miny = mn.ky; P.mini = mn.i;
       P.maxx = mx.kx; P.maxy = mx.ky; P.maxi = mx.i;
       P.flags = fl;
       P.pad = 0;
-#pragma unroll
-      for (int k = 0; k < 6; k++) {
-        P.ov[k] = oc.v[k];
-        P.oi[k] = oc.i[k];
-      }
       w.k0part[t] = P;
     }
     __syncthreads();
@@ -433,32 +359,43 @@ __global__ void __launch_bounds__(kK0Threads) k_k0(Work w) {
 // One warp per point set: p, q, the set's flags; emit p; make the level-0
 // segment (a = p, b = p, r = q), whose children are p->q (upper, points left
 // of p->q) and q->p (lower), the two calls of Alg. 1's first line.
-__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl,
-                              const K0Oct& oc, int lane);
+__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl, int lane);
 
-// One block per point set: the set's tile partials are reduced by the whole
+// One block per point set: the set's partials are reduced by the whole
 // block, then warp 0 finishes the set.
 __global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
   __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
   __shared__ int s_fl[kK0Threads / kWarp];
-  __shared__ K0Oct s_oc[kK0Threads / kWarp];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int s = blockIdx.x; s < w.nsets; s += gridDim.x) {
     SetRec S = w.sets[s];
     if (S.len == 0) continue;  // uniform across the block
     LexPt mn{LLONG_MAX, LLONG_MAX, INT_MAX}, mx{LLONG_MIN, LLONG_MIN, INT_MAX};
     int fl = 0;
-    K0Oct oc;
-    oct_init(oc);
+    // partials: one per extreme-pass tile, or (sieve) one per sieve block
+    // that worked on the set, block g of G at slot g + s, where block g
+    // holds tiles [T g / G, T (g + 1) / G): the blocks of the set's first
+    // and last tiles u are ceil((u + 1) G / T) - 1, and the empty ones
+    // between them wrote nothing
+    long long lo = w.k0_tile_start[s], hi = w.k0_tile_start[s + 1];
+    const long long T = w.k0_tile_start[w.nsets], G = w.sieve ? __ldcg(&w.ctrl->sv_grid) : 0;
+    if (w.sieve) {
+      if (hi <= lo || G <= 0) {
+        lo = hi = 0;
+      } else {
+        const long long g0 = ((lo + 1) * G + T - 1) / T - 1, g1 = (hi * G + T - 1) / T - 1;
+        lo = g0;
+        hi = g1 + 1;
+      }
+    }
 #pragma unroll 4
-    for (int t = w.k0_tile_start[s] + threadIdx.x; t < w.k0_tile_start[s + 1]; t += kK0Threads) {
-      const K0Part P = w.k0part[t];
+    for (long long t = lo + threadIdx.x; t < hi; t += kK0Threads) {
+      if (w.sieve && T * (t + 1) / G <= T * t / G) continue;  // block t had no tile
+      const K0Part P = w.k0part[w.sieve ? t + s : t];
       const LexPt a{P.minx, P.miny, P.mini}, b{P.maxx, P.maxy, P.maxi};
       if (lex_min_better(a, mn)) mn = a;
       if (lex_max_better(b, mx)) mx = b;
       fl |= P.flags;
-#pragma unroll
-      for (int k = 0; k < 6; k++) oct_merge(oc, k, P.ov[k], P.oi[k]);
     }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
@@ -467,15 +404,12 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
       if (lex_max_better(b, mx)) mx = b;
       fl |= __shfl_xor_sync(kFull, fl, m);
     }
-    oct_warp_reduce(oc);
-    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; s_oc[warp] = oc; }
+    if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; s_fl[warp] = fl; }
     __syncthreads();
     if (warp == 0) {
       mn = lane < kK0Threads / kWarp ? s_mn[lane] : LexPt{LLONG_MAX, LLONG_MAX, INT_MAX};
       mx = lane < kK0Threads / kWarp ? s_mx[lane] : LexPt{LLONG_MIN, LLONG_MIN, INT_MAX};
       fl = lane < kK0Threads / kWarp ? s_fl[lane] : 0;
-      if (lane < kK0Threads / kWarp) oc = s_oc[lane];
-      else oct_init(oc);
 #pragma unroll
       for (int m = 16; m >= 1; m >>= 1) {
         const LexPt a = shfl_lex(mn, m), b = shfl_lex(mx, m);
@@ -483,170 +417,55 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
         if (lex_max_better(b, mx)) mx = b;
         fl |= __shfl_xor_sync(kFull, fl, m);
       }
-      oct_warp_reduce(oc);
-      k0_finish_set(w, s, S, mn, mx, fl, oc, lane);
+      k0_finish_set(w, s, S, mn, mx, fl, lane);
     }
     __syncthreads();  // the shared partials are reused by the next set
   }
 }
 
-// Level-0 pre-filter chains of one point set (see OctF).  Side 0 is the
-// sequence p, c0, c1, c2, q (the candidates extreme in y - x, y, x + y),
-// side 1 is q, c3, c4, c5, p.  Lanes 0..19 evaluate the exact orientation
-// of every ordered triple of positions i < j < k of both sequences; lane 0
-// then builds each chain like one half of Andrew's monotone chain: a
-// candidate is kept if it is strictly left of the side's base line (p->q or
-// q->p) and strictly further along x than the chain's last vertex, after
-// popping vertices that would not make a strict right turn.  Returns (in
-// every lane) whether some chain has an inner vertex; `of` is valid in lane 0.
-__device__ int oct_seq(int side, int pos, int p, int q, const K0Oct& oc) {
-  if (pos == 0) return side ? q : p;
-  if (pos == 4) return side ? p : q;
-  return oc.i[3 * side + pos - 1];
-}
-__device__ __forceinline__ int oct_tri(int i, int j, int k) {  // index of (i < j < k) among the 10 triples of 0..4
-  const int base_i[4] = {0, 6, 9, 10};  // triples starting at i: C(4-i, 2), cumulated
-  const int base_j[5] = {0, 0, 3, 5, 6};
-  return base_i[i] + (base_j[j] - base_j[i + 1]) + (k - j - 1);
-}
-__device__ bool build_oct(const Work& w, int p, int q, const K0Oct& oc, OctF& of, int lane) {
-  int sgn = 0;
-  if (lane < 20) {
-    const int side = lane / 10, t = lane % 10;
-    int ti = 0, tj = 1, tk = 2, c = 0;
-    for (int i = 0; i < 5; i++)
-      for (int j = i + 1; j < 5; j++)
-        for (int k = j + 1; k < 5; k++) {
-          if (c == t) { ti = i; tj = j; tk = k; }
-          c++;
-        }
-    const int a = oct_seq(side, ti, p, q, oc), b = oct_seq(side, tj, p, q, oc), d = oct_seq(side, tk, p, q, oc);
-    if (a >= 0 && a < w.N && b >= 0 && b < w.N && d >= 0 && d < w.N)
-      sgn = orient_sign_slow(w.x[a], w.y[a], w.x[b], w.y[b], w.x[d], w.y[d]);
-  }
-  int tab[20];
-#pragma unroll
-  for (int t = 0; t < 20; t++) tab[t] = __shfl_sync(kFull, sgn, t);
-  int on = 0;
-  int ev[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // polygon vertices in clockwise order, closed: ev[ne] = ev[0]
-  int ne = 0;
-  if (lane == 0) {
-    for (int side = 0; side < 2; side++) {
-      const int* T = tab + 10 * side;
-      const double sx = side ? -1.0 : 1.0;
-      const double bx = w.x[oct_seq(side, 4, p, q, oc)];
-      int st[5];
-      int n = 0;
-      st[n++] = 0;
-      for (int pos = 1; pos <= 3; pos++) {
-        const int idx = oct_seq(side, pos, p, q, oc);
-        if (idx < 0 || idx >= w.N) continue;
-        if (!(T[oct_tri(0, pos, 4)] < 0)) continue;  // orient(A, B, c) > 0: strictly outside the base line
-        const double cx = w.x[idx], lx = w.x[oct_seq(side, st[n - 1], p, q, oc)];
-        if (!(sx * cx > sx * lx && sx * cx < sx * bx)) continue;
-        while (n >= 2 && T[oct_tri(st[n - 2], st[n - 1], pos)] >= 0) n--;
-        st[n++] = pos;
-      }
-      while (n >= 2 && T[oct_tri(st[n - 2], st[n - 1], 4)] >= 0) n--;
-      st[n++] = 4;
-      for (int i = 0; i + 1 < n; i++) ev[ne++] = oct_seq(side, st[i], p, q, oc);
-      const int k = n - 2;  // inner vertices st[1 .. n-2]
-      OctSide& S = of.s[side];
-      S.sx = side ? -1.0f : 1.0f;
-      for (int i = 0; i < 3; i++)
-        S.t[i] = i < k ? S.sx * trunc_f32(w.x[oct_seq(side, st[i + 1], p, q, oc)]) : INFINITY;
-      for (int j = 0; j < 4; j++) {
-        if (j <= k) {
-          const int a = oct_seq(side, st[j], p, q, oc), b = oct_seq(side, st[j + 1], p, q, oc);
-          S.e[j] = make_line(w.x[a], w.y[a], w.x[b], w.y[b]);
-        } else {
-          S.e[j] = LineF{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        }
-      }
-      if (k >= 1) on = 1;
-    }
-    ev[ne] = ev[0];
-  }
-  // the inner box: x from the larger of the upper-left / lower-left
-  // candidates' x to the smaller of the upper-right / lower-right ones', y
-  // likewise; kept if its four corners lie in the closed polygon (lane k
-  // checks corner k / 8 against edge k % 8 exactly)
-  ne = __shfl_sync(kFull, ne, 0);
-  int efrom = 0, eto = 0;
-#pragma unroll
-  for (int e = 0; e < 8; e++) {
-    const int f = __shfl_sync(kFull, ev[e], 0), t = __shfl_sync(kFull, ev[e + 1], 0);
-    if ((lane & 7) == e) { efrom = f; eto = t; }
-  }
-  const int iul = oc.i[0], iur = oc.i[2], ilr = oc.i[3], ill = oc.i[5];
-  bool ok = __shfl_sync(kFull, on, 0) != 0 && iul >= 0 && iul < w.N && iur >= 0 && iur < w.N && ilr >= 0 &&
-            ilr < w.N && ill >= 0 && ill < w.N;
-  double bx0 = 0.0, bx1 = 0.0, by0 = 0.0, by1 = 0.0;
-  if (ok) {
-    bx0 = fmax(w.x[iul], w.x[ill]);
-    bx1 = fmin(w.x[iur], w.x[ilr]);
-    by0 = fmax(w.y[ill], w.y[ilr]);
-    by1 = fmin(w.y[iul], w.y[iur]);
-    ok = bx0 < bx1 && by0 < by1;
-  }
-  if (ok && (lane & 7) < ne) {
-    const int corner = lane >> 3;
-    const double cx = (corner == 1 || corner == 2) ? bx1 : bx0, cy = corner >= 2 ? by1 : by0;
-    ok = orient_sign_slow(w.x[efrom], w.y[efrom], w.x[eto], w.y[eto], cx, cy) <= 0;
-  }
-  ok = __all_sync(kFull, ok);
-  if (lane == 0) {
-    of.bx0 = ok ? trunc_f32(bx0) : INFINITY;
-    of.bx1 = ok ? trunc_f32(bx1) : -INFINITY;
-    of.by0 = ok ? trunc_f32(by0) : INFINITY;
-    of.by1 = ok ? trunc_f32(by1) : -INFINITY;
-  }
-  return __shfl_sync(kFull, on, 0) != 0;
-}
-
 // Warp 0 of the finalize block: p, q and the flags of set s; emit p; make
-// the level-0 segment.
-__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl,
-                              const K0Oct& oc, int lane) {
-  {
-    if (fl & 1) {
-      if (lane == 0) {
-        atomicOr(&w.ctrl->err, kErrNonfinite);
-        atomicMin(reinterpret_cast<unsigned long long*>(&w.ctrl->nonfinite_set), (unsigned long long)s);
-      }
-      return;
-    }
-    const int p = mn.i, q = mx.i;
-    S.p = p;
-    S.q = q;
-    S.flags = (fl & 2) ? 0 : kSegFast;
-    if ((fl & 2) && lane == 0) atomicOr(&w.ctrl->any_slow, 1);
+// the level-0 segment.  On the pre-filter path the segment holds the
+// sieve's survivors of the set, in buffer 1 from the set's offset; p and q
+// are among them (strict vertices are never dropped), so the extremes of
+// the survivors are those of the set.
+__device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, const LexPt& mx, int fl, int lane) {
+  if (fl & 1) {
     if (lane == 0) {
-      w.sets[s] = S;
-      emit(w, (long long)S.off + S.shift, p - S.off);
+      atomicOr(&w.ctrl->err, kErrNonfinite);
+      atomicMin(reinterpret_cast<unsigned long long*>(&w.ctrl->nonfinite_set), (unsigned long long)s);
     }
-    if (p == q) return;  // all points coincide with p
-    SegRec R;
-    R.shift = S.shift;
-    R.off = S.off;
-    R.len = S.len;
-    R.a = p;
-    R.b = p;
-    R.r = q;
-    R.set_off = S.off;
-    R.level = 0;
-    R.tile_base = 0;
-    R.ntiles = 0;
-    R.flags = S.flags | kSegSrcInput;
-    if (S.len <= w.small_max) {
-      if (lane == 0) push_k3(w, R);
-    } else {
-      OctF of;
-      const bool on = w.oct && w.prefilter && (S.flags & kSegFast) && build_oct(w, p, q, oc, of, lane);
-      if (on) R.flags |= kSegOct;
-      const int slot = push_k1_warp(w, 0, R, lane);
-      if (on && lane == 0 && slot >= 0 && slot < w.nsets) w.oct[slot] = of;
-    }
+    return;
+  }
+  const int p = mn.i, q = mx.i;
+  if (p < S.off || p >= S.off + S.len || q < S.off || q >= S.off + S.len) {  // partials not written: an earlier error
+    if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
+    return;
+  }
+  S.p = p;
+  S.q = q;
+  S.flags = (fl & 2) ? 0 : kSegFast;
+  if ((fl & 2) && lane == 0) atomicOr(&w.ctrl->any_slow, 1);
+  if (lane == 0) {
+    w.sets[s] = S;
+    emit(w, (long long)S.off + S.shift, p - S.off);
+  }
+  if (p == q) return;  // all points coincide with p
+  SegRec R;
+  R.shift = S.shift;
+  R.off = S.off;
+  R.len = w.sieve ? min(__ldcg(&w.nsurv[s]), S.len) : S.len;
+  R.a = p;
+  R.b = p;
+  R.r = q;
+  R.set_off = S.off;
+  R.level = 0;
+  R.tile_base = 0;
+  R.ntiles = 0;
+  R.flags = S.flags | (w.sieve ? kSegSrcBuf1 : kSegSrcInput);
+  if (R.len <= w.small_max) {
+    if (lane == 0) push_k3(w, R);
+  } else {
+    push_k1_warp(w, 0, R, lane);
   }
 }
 
@@ -672,6 +491,13 @@ __global__ void k_prologue(Work w, int level) {
 // condition stops with a timeout (far beyond any real run: a 1e8-point
 // hull-dense input takes under a second).
 constexpr unsigned long long kLevelLoopNs = 60ull * 1000000000ull;
+
+// First test of the device-driven level loop: run it only if level 0 left
+// segments for level 1 and raised no fatal error.
+__global__ void k_loop_init(Work w, cudaGraphConditionalHandle h) {
+  const Ctrl* c = w.ctrl;
+  cudaGraphSetConditional(h, (c->k1_segs[1] > 0 && !(c->err & kErrFatal)) ? 1u : 0u);
+}
 
 __global__ void k_level_cond(Work w, cudaGraphConditionalHandle h, long long max_iters) {
   Ctrl* c = w.ctrl;
@@ -1121,6 +947,7 @@ __global__ void __launch_bounds__(kK1Threads) k_k1(Work w, int level) {
 }
 
 #include "vq_partition.cuh"
+#include "vq_sieve.cuh"
 
 // ---------------------------------------------------------------------------
 // K2: per segment, cross-tile argmax, emission, children
@@ -1578,24 +1405,36 @@ __global__ void __launch_bounds__(256) k_k4_write(const unsigned* bm, long long 
   }
 }
 
-__device__ __forceinline__ long long key_rank(const unsigned* bm, long long nwords, const long long* sums,
-                                              long long key) {
+// Rank of a key among the emitted ones (set bits below it), one warp per
+// key: the block prefix plus the bits of the words before it in its block.
+__device__ __forceinline__ long long key_rank_warp(const unsigned* bm, long long nwords, const long long* sums,
+                                                   long long key, int lane) {
   const long long word = key >> 5;
   const long long blk = word / kK4Words;
-  long long r = sums[blk];
-  for (long long q = blk * kK4Words; q < word && q < nwords; q++) r += __popc(bm[q]);
+  long long r = 0;
+  for (long long q = blk * kK4Words + lane; q < word && q < nwords; q += kWarp) r += __popc(bm[q]);
+  r = warp_sum_ll(r);
+  r += sums[blk];
   if (word < nwords) r += __popc(bm[word] & ((1u << (unsigned)(key & 31)) - 1u));
   return r;
 }
 
-__global__ void k_k4_offsets(Work w, const long long* sums, long long* hull_offsets, long long* total) {
+// hull_offsets[s] = rank of set s's first key (one warp per set); the
+// total is the scan's last entry.
+__global__ void k_k4_offsets(Work w, const long long* sums, long long nb, long long* hull_offsets, long long* total) {
   const long long nwords = (w.nkeys + 31) >> 5;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s > w.nsets) return;
-  const long long key = s < w.nsets ? (long long)w.sets[s].off + w.sets[s].shift : w.nkeys;
-  const long long r = key_rank(w.bitmap, nwords, sums, key);
-  if (hull_offsets) hull_offsets[s] = r;
-  if (s == w.nsets && total) *total = r;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  if (gw == 0 && lane == 0) {
+    if (total) *total = sums[nb];
+    if (hull_offsets) hull_offsets[w.nsets] = sums[nb];
+  }
+  if (!hull_offsets) return;
+  for (int s = gw; s < w.nsets; s += nw) {
+    const long long key = (long long)w.sets[s].off + w.sets[s].shift;
+    const long long r = key_rank_warp(w.bitmap, nwords, sums, key, lane);
+    if (lane == 0) hull_offsets[s] = r;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1690,6 +1529,12 @@ cudaError_t launch_seed(const Work& w, cudaStream_t st) {
 
 static int device_sms();
 
+// upper bound of the extreme-pass tiles (exact for one set)
+static long long k0_tiles_bound(const Work& w) {
+  return w.offsets ? (long long)w.N / kK0Tile + w.nsets : (w.n_single + kK0Tile - 1) / kK0Tile;
+}
+
+
 static constexpr int k0_ring_bytes() { return (int)(sizeof(double2) * kK0Stages * 2 * kK0Pairs * kK0Threads); }
 
 // Extreme pass: a resident grid, sized so that every block gets the same
@@ -1708,7 +1553,7 @@ cudaError_t launch_k0(const Work& w, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     occ[dev] = n > 0 ? n : 1;
   }
-  const long long tiles = w.offsets ? (long long)w.N / kK0Tile + w.nsets : (w.n_single + kK0Tile - 1) / kK0Tile;
+  const long long tiles = k0_tiles_bound(w);
   long long g = (long long)occ[dev] * device_sms();
   if (tiles < g) g = tiles;
   if (g < 1) g = 1;
@@ -1728,6 +1573,46 @@ cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_sample(const Work& w, cudaStream_t st) {
+  long long g = (long long)device_sms() * 8;
+  const long long units = (k0_tiles_bound(w) / kSampleEvery + 1 + w.nsets) * kSampleParts;
+  if (g > units) g = units;
+  if (g < 1) g = 1;
+  count_launch();
+  k_sample<<<(unsigned)g, 256, 0, st>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poly(const Work& w, cudaStream_t st) {
+  long long g = ((long long)w.nsets + 3) / 4;
+  if (g > 2048) g = 2048;
+  if (g < 1) g = 1;
+  count_launch();
+  k_poly<<<(unsigned)g, 128, 0, st>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sieve(const Work& w, cudaStream_t st) {
+  static int occ[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  constexpr int threads = 32 * kSvWarps;
+  if (occ[dev] == 0) {
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sieve, threads, 0);
+    if (e != cudaSuccess) return e;
+    occ[dev] = n > 0 ? n : 1;
+  }
+  long long g = (long long)occ[dev] * device_sms();
+  const long long tiles = k0_tiles_bound(w);
+  if (g > tiles) g = tiles;
+  if (g > kSvMaxBlocks) g = kSvMaxBlocks;
+  if (g < 1) g = 1;
+  count_launch();
+  k_sieve<<<(unsigned)g, threads, 0, st>>>(w);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, long long max_iters, cudaStream_t st) {
   count_launch();
   k_level_cond<<<1, 1, 0, st>>>(w, h, max_iters);
@@ -1735,6 +1620,19 @@ cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, long 
 }
 
 void count_launches(long long k) { count_launch((int)k); }
+
+cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphNode_t* node, const Work& w, cudaGraphConditionalHandle h) {
+  Work wc = w;
+  void* args[2] = {&wc, &h};
+  cudaKernelNodeParams p = {};
+  p.func = reinterpret_cast<void*>(k_loop_init);
+  p.gridDim = dim3(1);
+  p.blockDim = dim3(1);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, nullptr, 0, &p);
+}
 
 cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st) {
   count_launch();
@@ -1774,7 +1672,7 @@ static cudaError_t launch_k1_ppt(const Work& w, int level, int grid, cudaStream_
   cfg.attrs = nullptr;
   cfg.numAttrs = 0;
   count_launch();
-  if (level == 0) return cudaLaunchKernelEx(&cfg, k_k1<PPT, true>, w, level);
+  if (level == 0 && !w.sieve) return cudaLaunchKernelEx(&cfg, k_k1<PPT, true>, w, level);
   return cudaLaunchKernelEx(&cfg, k_k1<PPT, false>, w, level);
 }
 
@@ -1837,7 +1735,7 @@ static cudaError_t launch_k1w_ppt(const Work& w, int level, int tiles, cudaStrea
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   count_launch();
-  if (level == 0)
+  if (level == 0 && !w.sieve)
     k_k1w<PPT, WPB, NS, true, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
   else
     k_k1w<PPT, WPB, NS, false, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
@@ -1846,6 +1744,10 @@ static cudaError_t launch_k1w_ppt(const Work& w, int level, int tiles, cudaStrea
 
 template <int PPT>
 static cudaError_t launch_k1w_sel(const Work& w, int level, int tiles, cudaStream_t st) {
+  if (w.tier_dev) {  // both; the device's flag lets one of them work
+    const cudaError_t e = launch_k1w_ppt<PPT, true>(w, level, tiles, st);
+    return e != cudaSuccess ? e : launch_k1w_ppt<PPT, false>(w, level, tiles, st);
+  }
   return w.all_fast ? launch_k1w_ppt<PPT, true>(w, level, tiles, st) : launch_k1w_ppt<PPT, false>(w, level, tiles, st);
 }
 
@@ -1961,9 +1863,10 @@ cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long 
   if (e != cudaSuccess) return e;
   count_launch();
   k_k4_write<<<(unsigned)nb, 256, 0, st>>>(w.bitmap, nwords, sums, w.slot, out, (long long)w.N, w.ctrl);
-  const int blocks = (w.nsets + 1 + 255) / 256;
+  long long blocks = ((long long)w.nsets + 7) / 8;
+  if (blocks > 1024) blocks = 1024;
   count_launch();
-  k_k4_offsets<<<blocks, 256, 0, st>>>(w, sums, hull_offsets, total);
+  k_k4_offsets<<<(unsigned)blocks, 256, 0, st>>>(w, sums, nb, hull_offsets, total);
   return cudaGetLastError();
 }
 

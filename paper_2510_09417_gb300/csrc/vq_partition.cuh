@@ -99,14 +99,12 @@ struct alignas(16) K1Stage {
 };
 static_assert(sizeof(SegGeom) == 96, "SegGeom is bulk-copied as 96 bytes");
 
-// A warp's private region: its stages and their mbarriers, and (level 0)
-// the pre-filter chains of the segment it is working on.
+// A warp's private region: its stages and their mbarriers.
 template <int PPT, int NS>
 struct alignas(16) K1Ring {
   static constexpr int TW = 32 * PPT;
   K1Stage<TW> st[NS];
   unsigned long long full[NS];
-  OctF oct;
 };
 
 // Pass-A classification.  FP32 tier: both lines are evaluated without
@@ -302,7 +300,7 @@ __device__ __forceinline__ void k1w_flush(const Work& w, int par, K1Run& r, int 
 
 template <int PPT, bool SRC_INPUT, bool FAST>
 __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PPT>* __restrict__ sg, int lane,
-                                         K1Run& run, unsigned long long* prof, OctF* soct) {
+                                         K1Run& run, unsigned long long* prof) {
   (void)prof;
   K1_MARK(c0);
   typedef typename KeyOf<FAST>::T K;
@@ -315,22 +313,12 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
   const int* I = sg->i + (sg->m.si & 3);
   const SegGeom* G = &sg->g;
   SegState* ss = &w.sstate[par][sid];
-  // level 0: the segment's pre-filter chains (the tile's flags say whether
-  // it has them; a level-0 segment's slot is below nsets)
-  const bool oct = SRC_INPUT && FAST && (sg->m.flags & kSegOct) != 0 && sid < w.nsets;
   if (sid != run.sid) {
     k1w_flush(w, par, run, lane);
     run.sid = sid;
     run.rb[0] = cand_none<double>();
     run.rb[1] = cand_none<double>();
     run.lf[0] = run.lf[1] = run.hf[0] = run.hf[1] = 0.0f;
-    if (oct) {
-      constexpr int NW = (int)(sizeof(OctF) / sizeof(int));
-      const int* src = reinterpret_cast<const int*>(w.oct + sid);
-      int* dst = reinterpret_cast<int*>(soct);
-      for (int i = lane; i < NW; i += kWarp) dst[i] = __ldcg(src + i);
-      __syncwarp();
-    }
   }
   run.t_last = t;
   if (lane == 0) {  // no record in this tile unless the run ends here
@@ -353,50 +341,13 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
     if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); }
     if (c == 2) { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); }
   };
-  bool filtered = false;
-  if constexpr (SRC_INPUT && FAST) {
-    if (oct) {
-      // level 0 with the pre-filter: the points certainly inside the inner
-      // box are dropped first (branch-free, four compares), then the rest
-      // are tested against the chain polygon, and only its survivors, a
-      // few per lane, are classified
-      unsigned rest = 0;
-      if (count == TW) {  // full tile: no per-point guard
 #pragma unroll
-        for (int k = 0; k < PPT; k++)
-          if (!oct_in_box(*soct, X[k * kWarp + lane], Y[k * kWarp + lane])) rest |= 1u << k;
-      } else {
-#pragma unroll
-        for (int k = 0; k < PPT; k++) {
-          const int l = k * kWarp + lane;
-          if (l < count && !oct_in_box(*soct, X[l], Y[l])) rest |= 1u << k;
-        }
-      }
-      unsigned keep = 0;
-      for (unsigned u = rest; u != 0; u &= u - 1) {
-        const int k = __ffs(u) - 1;
-        const int l = k * kWarp + lane;
-        if (!oct_inside(*soct, X[l], Y[l])) keep |= 1u << k;
-      }
-      for (unsigned u = keep; u != 0; u &= u - 1) {
-        const int k = __ffs(u) - 1;
-        const int l = k * kWarp + lane;
-        K key, err;
-        const int c = classify_a(*G, l1, l2, X[l], Y[l], key, err);
-        account(k, c, key, err);
-      }
-      filtered = true;
-    }
-  }
-  if (!filtered) {
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-      const int l = k * kWarp + lane;
-      if (l < count) {
-        K key, err;
-        const int c = classify_a(*G, l1, l2, X[l], Y[l], key, err);
-        account(k, c, key, err);
-      }
+  for (int k = 0; k < PPT; k++) {
+    const int l = k * kWarp + lane;
+    if (l < count) {
+      K key, err;
+      const int c = classify_a(*G, l1, l2, X[l], Y[l], key, err);
+      account(k, c, key, err);
     }
   }
   // exact tiers for the undecided points (rare)
@@ -548,6 +499,8 @@ __global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Wor
   const int par = level & 1;
   // warps are independent from here on: each may leave on its own
   if (fatal(w)) return;
+  // launched beside its other instantiation: the device's tier flag picks one
+  if (w.tier_dev && ALLFAST == (*reinterpret_cast<volatile int*>(&w.ctrl->any_slow) != 0)) return;
   Ring* R = reinterpret_cast<Ring*>(k1w_smem) + warp;
   const int ntiles = min(*reinterpret_cast<volatile int*>(&w.ctrl->k1_tiles[par]), w.capT);
   const long long gw = (long long)blockIdx.x * WPB + warp, nw = (long long)gridDim.x * WPB;
@@ -597,9 +550,9 @@ __global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Wor
     }
     K1Stage<32 * PPT>* sg = &R->st[s];
     if (ALLFAST || (sg->m.flags & kSegFast))
-      k1w_tile<PPT, SRC_INPUT, true>(w, par, sg, lane, run, prof, &R->oct);
+      k1w_tile<PPT, SRC_INPUT, true>(w, par, sg, lane, run, prof);
     else
-      k1w_tile<PPT, SRC_INPUT, ALLFAST>(w, par, sg, lane, run, prof, &R->oct);
+      k1w_tile<PPT, SRC_INPUT, ALLFAST>(w, par, sg, lane, run, prof);
     __syncwarp();
     K1_MARK(i0);
     if (lane == 0 && t_issue < t_end) {

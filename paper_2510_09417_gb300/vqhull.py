@@ -58,6 +58,7 @@ class Profile(ctypes.Structure):
         ("k4_ms", ctypes.c_double),
         ("other_ms", ctypes.c_double),
         ("graph_launches", ctypes.c_int64),
+        ("sample_ms", ctypes.c_double),
     ]
 
 

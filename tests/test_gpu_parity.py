@@ -188,7 +188,8 @@ def test_lookback_timeout_is_reported(vq):
     bounded waits expire; the call reports VQ_ERR_TIMEOUT and the device
     stays usable."""
     x, y = synth.points("square", 400_000, 3)
-    vq.vq_set_config(ordered=1, debug_drop_tile=2, timeout_ns=20_000_000)
+    # prefilter off: level 0 then partitions all 400K points in ordered mode
+    vq.vq_set_config(ordered=1, debug_drop_tile=2, timeout_ns=20_000_000, prefilter=0)
     with pytest.raises(vq.VQError) as e:
         gpu_hull(vq, x, y)
     assert e.value.status == -6
@@ -313,12 +314,12 @@ def test_device_level_loop_batched(vq):
 
 @pytest.mark.parametrize("dist", synth.DISTRIBUTIONS)
 def test_prefilter(vq, dist):
-    """The level-0 pre-filter (points certainly inside the polygon of the
-    extreme pass's candidates are dropped) leaves every hull unchanged and
-    only removes points: level 0 keeps no more points than plain Alg. 1,
-    and far fewer on the square and the disk, where the polygon covers
-    most of the set.  The later levels see a subset of the plain run's
-    points."""
+    """The level-0 pre-filter (the sieve drops the points certainly inside
+    the chains of sampled extremes before level 0) leaves every hull
+    unchanged and only removes points: level 0 reads no more points than
+    plain Alg. 1, and far fewer on the square and the disk, where the chains
+    cover most of the set.  The later levels see a subset of the plain
+    run's points."""
     x, y = synth.points(dist, 2_000_000, 77)
     want = oracle.hull(x, y)
     vq.vq_set_config(prefilter=0)
@@ -327,11 +328,12 @@ def test_prefilter(vq, dist):
     vq.vq_set_config(prefilter=1)
     assert np.array_equal(gpu_hull(vq, x, y), want)
     filt = vq.vq_last_stats()
-    assert filt["read"][0] == plain["read"][0] == 2_000_000
+    assert plain["read"][0] == 2_000_000
+    assert filt["read"][0] <= plain["read"][0]
     assert filt["written"][0] <= plain["written"][0]
     assert sum(filt["read"]) <= sum(plain["read"])
     if dist in ("square", "disk"):
-        assert filt["written"][0] < 0.2 * plain["written"][0]
+        assert filt["read"][0] < 0.05 * plain["read"][0]
 
 
 def test_prefilter_degenerate_candidates(vq):
