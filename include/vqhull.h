@@ -79,7 +79,10 @@ vq_status vq_hull2d(const double* x, const double* y, int64_t n, int32_t* hull_i
                     void* stream);
 
 /*
- * Hulls of nsets independent point sets in one level-synchronous run.
+ * Hulls of nsets independent point sets in one level-synchronous run: the
+ * result per set is that of Alg. 1 (Sec. 2.1), and every level of the
+ * subset extraction (Sec. 3: classify, compact, farthest point) runs over
+ * the live segments of all sets at once.
  *   x, y          device FP64 arrays holding the sets back to back
  *   offsets       device int64[nsets + 1]: set s is points
  *                 offsets[s] .. offsets[s+1]-1; offsets[0] = 0, non-decreasing;
@@ -107,14 +110,14 @@ vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, 
 /*
  * vq_hull2d for callers that cannot allocate.  The paper has no counterpart:
  * this entry point exists for code that must not trigger a device or host
- * allocation from inside a library call -- work recorded while a CUDA graph
- * is being captured, hosts that forbid allocation after start-up, and
- * processes whose device memory is handed out by their own pool allocator.
- * It runs the same kernels as vq_hull2d (with the host-driven level loop
- * and without the level-0 pre-filter, which changes no hull), but its whole
- * workspace is one fixed 64 MiB array of device memory that is part of this
- * library; every GPU that loads the library reserves it until the process
- * exits.  The call
+ * allocation from inside a library call -- hosts that forbid allocation
+ * after start-up (an allocation can stall or fail at an unpredictable
+ * moment) and processes whose device memory is handed out by their own pool
+ * allocator, which must account for every byte.  It runs the same kernels
+ * as vq_hull2d (with the host-driven level loop and without the level-0
+ * pre-filter, which changes no hull), but its whole workspace is one fixed
+ * 64 MiB array of device memory that is part of this library; every GPU
+ * that loads the library reserves it until the process exits.  The call
  * makes no cudaMalloc, cudaMallocHost, cudaFree or other allocating call.
  *   x, y, hull_idx, h, stream   as for vq_hull2d (hull_idx: room for n)
  *   n                           0 <= n <= 1,048,576; larger n returns
@@ -125,7 +128,8 @@ vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, 
  * which keeps the previous call's contents (each call clears what it needs
  * zeroed); calls that overlap on the GPU would race on it.  This function
  * therefore takes a process-wide lock and waits for `stream` before it
- * returns, so calls made through it never overlap.
+ * returns (also when it fails), so calls made through it never overlap.
+ * Device waits are bounded by vq_config.timeout_ns, as for vq_hull2d.
  */
 vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t n, int32_t* hull_idx, int64_t* h,
                             void* stream);
@@ -231,7 +235,9 @@ typedef struct {
 
 /*
  * Creates a server: continuous batching of hull requests (the level-
- * synchronous extraction of Sec. 3 applied to many requests at once).
+ * synchronous extraction of Sec. 3 applied to many requests at once).  The
+ * paper has no counterpart for serving; each request's result is the hull
+ * of Alg. 1 (Sec. 2.1), the same as vq_hull2d's on the same points.
  * Each of `lanes` host threads owns a CUDA stream and a hull context.  An
  * idle lane takes the queued requests (FIFO) that fit the free request
  * slots (max_inflight) and the free device memory (mem_budget_bytes),
@@ -246,13 +252,17 @@ typedef struct {
 vq_status vq_server_create(const vq_server_config* cfg, vq_server** out);
 
 /* Queues a hull of n host points (copied before return; the caller may free
- * them).  VQ_ERR_BUDGET if the request alone exceeds the memory budget. */
+ * them).  VQ_ERR_BUDGET if the request alone (its batch's device bytes plus
+ * the server's fixed 1 MiB reserve) exceeds the memory budget.  Serving
+ * only; no counterpart in the paper. */
 vq_status vq_server_submit(vq_server* s, const double* x_host, const double* y_host, int64_t n,
                            uint64_t* ticket);
 
 /* VQ_OK with the result copied to hull_idx_host (room for cap indices; h set),
  * VQ_PENDING, VQ_ERR_CAPACITY if cap < h, VQ_ERR_NOT_FOUND, or the request's
- * own error.  A result is released once returned with VQ_OK. */
+ * own error.  A result is released once returned with VQ_OK.  The result is
+ * the hull of Alg. 1 (Sec. 2.1), clockwise from the lexicographic minimum,
+ * indices into the request's points. */
 vq_status vq_server_poll(vq_server* s, uint64_t ticket, int32_t* hull_idx_host, int64_t cap, int64_t* h);
 
 /* As vq_server_poll, waiting up to timeout_ms (< 0: no limit). */
@@ -268,7 +278,8 @@ vq_status vq_server_wait(vq_server* s, uint64_t ticket, int32_t* hull_idx_host, 
 vq_status vq_server_wait_any(vq_server* s, uint64_t* ticket, int32_t* hull_idx_host, int64_t cap, int64_t* h,
                              int32_t timeout_ms, double* latency_ms);
 
-/* Latency percentiles (submit to completion) and throughput so far. */
+/* Latency percentiles (submit to completion) and throughput so far
+ * (serving only; no counterpart in the paper). */
 vq_status vq_server_stats(vq_server* s, double* p50_ms, double* p99_ms, double* hulls_per_s);
 
 /* Counters of the server since its creation. */

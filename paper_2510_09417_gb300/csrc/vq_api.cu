@@ -38,6 +38,8 @@ static Config get_cfg() {
   return g_cfg;
 }
 
+long long config_timeout_ns() { return get_cfg().timeout_ns; }
+
 static vq_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return VQ_OK;
   if (e == cudaErrorMemoryAllocation) return VQ_ERR_NOMEM;

@@ -102,6 +102,9 @@ long long kernels_launched();  // kernels launched by this library so far (all d
 void count_launches(long long k);  // adds k (may be negative) to that count
 int k3_smem_bytes();
 
+// vq_config.timeout_ns as currently set (vq_api.cu)
+long long config_timeout_ns();
+
 // Hull contexts with caller-provided workspaces (vq_api.cu), used by the
 // server: each lane owns a context and runs its batches on its own stream.
 struct Ctx;

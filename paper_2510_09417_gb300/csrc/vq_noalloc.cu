@@ -2,13 +2,15 @@
 // must not allocate.
 //
 // Some callers cannot let a library call cudaMalloc (or cudaMallocHost, or
-// any allocating routine): code that runs while a CUDA graph is being
-// captured, real-time or embedded hosts that forbid allocation after start
-// up, and processes whose device memory is owned by a pool allocator that
-// must see every byte.  vq_hull2d allocates its workspace lazily, so this
-// entry point runs the same kernels out of one fixed block of device memory
-// instead: the file-scope array below.  It is part of the module, so every
-// GPU that loads this library reserves it (64 MiB) until the process exits.
+// any allocating routine): real-time or embedded hosts that forbid
+// allocation after start-up, because an allocation can stall or fail at
+// an unpredictable moment, and processes whose device memory is owned by a
+// pool allocator that must account for every byte.  vq_hull2d allocates its
+// workspace lazily, so this entry point runs the same kernels out of one
+// fixed block of device memory instead: the file-scope array below.  It is
+// part of the module, so every GPU that loads this library reserves it
+// (64 MiB) until the process exits.  The call waits for its stream before
+// it returns.
 //
 // The workspace for n points needs about 46 bytes per point plus tables;
 // kNoAllocMaxPoints (2^20) is the largest n that fits, and larger n is
@@ -27,7 +29,6 @@ constexpr long long kNoAllocMaxPoints = 1ll << 20;
 constexpr size_t kNoAllocBytes = 64ull << 20;
 constexpr int kNoAllocPPT = 16;          // partition tile: 32 lanes x 16 points
 constexpr int kNoAllocSmallMax = 1024;   // small-segment threshold
-constexpr long long kNoAllocTimeoutNs = 2000000000ll;
 
 // The scratch.  Host code must not use this name as an address: it has to
 // ask the runtime for the device address of the symbol (see setup()).
@@ -143,13 +144,17 @@ extern "C" vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t
   w.n_single = n;
   w.nsets = 1;
   w.N = (int)n;
-  w.timeout_ns = kNoAllocTimeoutNs;
+  w.timeout_ns = config_timeout_ns();  // the bound of vq_config, as on the allocating path
   w.drop_tile = -1;
   w.ordered = 0;
 
+  // on a failure, work already queued may still use the shared array: the
+  // stream is drained before the lock is released
 #define NA_CHECK(call)                                     \
   do {                                                     \
     if ((call) != cudaSuccess) {                           \
+      cudaGetLastError();                                  \
+      cudaStreamSynchronize(st);                           \
       cudaGetLastError();                                  \
       return VQ_ERR_CUDA;                                  \
     }                                                      \

@@ -119,8 +119,8 @@ static int admit_count(const vq_server* s, int limit, long long* points, size_t*
   if (limit > 0) nq = std::min(nq, limit);
   std::vector<int64_t> sizes((size_t)nq);
   for (int i = 0; i < nq; i++) sizes[(size_t)i] = s->queue[(size_t)i]->n;
-  return vq::admit_prefix(sizes.data(), nq, s->resident, s->used, s->cfg.max_inflight, s->cfg.mem_budget_bytes,
-                          batch_bytes, points, bytes);
+  return vq::admit_prefix(sizes.data(), nq, s->resident, s->used, kBytesFixed, s->cfg.max_inflight,
+                          s->cfg.mem_budget_bytes, batch_bytes, points, bytes);
 }
 
 // The queue's head can be admitted now (caller holds mu).

@@ -8,10 +8,10 @@
 static size_t model_bytes(long long points, int sets) { return (size_t)(68 * points + 1000 * sets); }
 
 static void run(const char* name, const int64_t* sizes, int nq, long long resident, size_t used, long long slots,
-                size_t budget) {
+                size_t budget, size_t reserve = 0) {
   long long pts = -1;
   size_t bytes = 0;
-  const int k = vq::admit_prefix(sizes, nq, resident, used, slots, budget, model_bytes, &pts, &bytes);
+  const int k = vq::admit_prefix(sizes, nq, resident, used, reserve, slots, budget, model_bytes, &pts, &bytes);
   std::printf("%s %d %lld %zu\n", name, k, pts, bytes);
 }
 
@@ -23,5 +23,9 @@ int main() {
   run("budget", q, 4, 0, 0, 64, 68 * 300 + 2000);     // the first two fit exactly
   run("head_too_big", q, 4, 0, 100000, 64, 100500);   // memory in use leaves too little
   run("empty", q, 0, 0, 0, 64, 1u << 30);
+  // the fixed reserve counts against the budget: the first two fit exactly
+  // with it, one byte less leaves room for the first only
+  run("reserve_fits", q, 4, 0, 5000, 64, 5000 + 68 * 300 + 2000 + 4096, 4096);
+  run("reserve_short", q, 4, 0, 5000, 64, 5000 + 68 * 300 + 2000 + 4095, 4096);
   return 0;
 }

@@ -168,8 +168,9 @@ def test_strictly_right_of_every_edge_means_strictly_inside():
 
 def test_server_admission_policy(tmp_path):
     """The serving handle's admission (vq_admit.h, host code): the longest
-    FIFO prefix within the free request slots and the memory budget,
-    nothing when the head does not fit.  Compiled with the host compiler."""
+    FIFO prefix within the free request slots and the memory budget (the
+    server's fixed reserve included), nothing when the head does not fit.
+    Compiled with the host compiler."""
     import os
     import shutil
     import subprocess
@@ -189,3 +190,5 @@ def test_server_admission_policy(tmp_path):
     assert got["budget"] == (2, 300, 68 * 300 + 2000)
     assert got["head_too_big"] == (0, 0, 0)
     assert got["empty"] == (0, 0, 0)
+    assert got["reserve_fits"] == (2, 300, 68 * 300 + 2000)
+    assert got["reserve_short"] == (1, 100, 68 * 100 + 1000)
