@@ -50,13 +50,53 @@ METRIC = "Gpoints/s & % HBM peak per hull; batched hulls/s, p50/p99 vs plain (bi
 UNIT = "Gpoints/s"
 WORKLOAD = "single hulls: uniform square + uniform disk, 1e8 FP64 SoA points each (seeds 1, 2)"
 FULL_N = 100_000_000
-# DRAM bytes the partition kernel moves per algorithmic unit (point
-# classified or kept), from one ncu capture of all six partition launches of
-# a 2e7-point disk hull with the level-0 pre-filter on (summarised under
-# profiles/): 456.6 MB read + 30.1 MB written for 26,605,189 points
-# classified and 6,637,667 kept.  Traffic grows in proportion to the units,
-# so a launch's traffic is this times its units.
-K1_DRAM_BYTES_PER_UNIT = 14.64
+# DRAM bytes the sieve moves per input point, from ncu captures of one
+# sieve launch on 2e7-point square and disk hulls (profiles/): the input is
+# read once (16 B per point) and the kept points are written.  Traffic grows
+# in proportion to the points, so a launch's traffic is this times n.
+SIEVE_DRAM_BYTES_PER_POINT = 16.2
+# DRAM bytes of every kernel of one hull per input point (ncu, all launches
+# of one 2e7-point hull; profiles/), per distribution.
+HULL_DRAM_BYTES_PER_POINT = {"square": 16.61, "disk": 17.47}
+
+
+def bench_configs(vq, torch, stream, dev, survivors, peak, reps=5):
+    """The workload list's single-hull configurations: square 1e6 (seed 1),
+    square / disk 1e8 (seeds 1 / 2, the step's inputs) and circle / Kuzmin 1e8
+    (seeds 3 / 4): median ms per hull over CUDA-event timed calls after a
+    warm-up, Gpoints/s, and the implementation model's bytes per hull (16 B
+    per point read by the sieve, 20 B per point it keeps, 20 B per point read
+    or kept at every level) over that time."""
+    out = {}
+    cases = [("1 square 1e6", "square", 1_000_000, None), ("2a square 1e8", "square", FULL_N, dev[0]),
+             ("2b disk 1e8", "disk", FULL_N, dev[1]), ("3a circle 1e8", "circle", FULL_N, None),
+             ("3b kuzmin 1e8", "kuzmin", FULL_N, None)]
+    for name, dist, n, d in cases:
+        if d is None:
+            x, y = synth.workload(dist, n, workers=WORKERS)
+            d = (torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+            del x, y
+        o = torch.empty(n, dtype=torch.int32, device="cuda")
+        vq.vq_hull2d(d[0], d[1], o, stream=stream)  # warm-up: workspace, graph
+        st = vq.vq_last_stats()
+        r = reps if dist != "circle" else 2
+        ts = []
+        for _ in range(r):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = vq.vq_hull2d(d[0], d[1], o, stream=stream).shape[0]
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        med = statistics.median(ts)
+        model = 16.0 * n + 20.0 * st["read"][0] + 20.0 * (sum(st["read"]) + sum(st["written"]))
+        out[name] = {"ms_per_hull": med, "gpoints_per_s": n / (med / 1e3) / 1e9, "h": int(h),
+                     "kept_by_sieve": int(st["read"][0]), "levels": int(st["levels"]),
+                     "model_bytes": model, "model_GBps": model / (med / 1e3) / 1e9,
+                     "model_frac": model / (med / 1e3) / 1e9 / peak, "samples": r}
+        del o
+    torch.cuda.empty_cache()
+    return out
 
 
 def parse():
@@ -78,11 +118,14 @@ def parse():
                     help="seconds of back-to-back steps for the energy figure (0: off)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration hull times")
     ap.add_argument("--serving-requests", type=int, default=128)
     ap.add_argument("--profile-one", default="", choices=[""] + list(synth.DISTRIBUTIONS),
                     help="profiling aid: run --profile-reps hulls of --n points of this distribution "
                          "(the workload's seed), print their counters and exit")
     ap.add_argument("--profile-reps", type=int, default=3)
+    ap.add_argument("--host-loop", action="store_true",
+                    help="profiling aid: levels launched from the host (profilers see every kernel)")
     return ap.parse_args()
 
 
@@ -95,6 +138,8 @@ def profile_one(args):
     import torch
     import paper_2510_09417_gb300 as vq
     vq.load()
+    if args.host_loop:
+        vq.vq_set_config(host_loop=1)
     x, y = synth.points(args.profile_one, args.n, SEEDS.get(args.profile_one, 1))
     xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
     del x, y
@@ -505,6 +550,10 @@ def main():
 
     for _ in range(max(args.warmup, 0)):
         hull_sizes = step()
+    survivors = []  # points the sieve kept per hull (level 0 reads them)
+    for (xd, yd), o in zip(dev, outs):
+        vq.vq_hull2d(xd, yd, o, stream=stream)
+        survivors.append(int(vq.vq_last_stats()["read"][0]))
     def timed(profile: bool):
         # K steps between a barrier and a synchronize on both sides, CUDA
         # events on the launching stream; with profile on, the library also
@@ -538,30 +587,47 @@ def main():
     pts_step = 2 * n * ws
     value = job_rate(2 * n * args.steps, ws, ms_max / 1e3) / 1e9
 
-    # roofline of the partition kernel: paper-model bytes / event time
+    # roofline of the dominant kernel, the sieve: 16 bytes read per point and
+    # 20 written per point it keeps (the level-0 reads), over its event time
     peak, peak_kind = peaks()
-    k1_bytes = 16.0 * (prof["k1_points_read"] + prof["k1_points_kept"])
-    k1_s = prof["k1_ms"] / 1e3
-    achieved = k1_bytes / k1_s / 1e9 if k1_s > 0 else 0.0
-    units_per_launch = (prof["k1_points_read"] + prof["k1_points_kept"]) / max(prof["k1_launches"], 1)
-    traffic = K1_DRAM_BYTES_PER_UNIT * units_per_launch
+    kept = sum(survivors) * args.steps
+    sv_bytes = 16.0 * 2 * n * args.steps + 20.0 * kept
+    sv_s = prof["k0_ms"] / 1e3
+    sv_launches = 2 * args.steps
+    achieved = sv_bytes / sv_s / 1e9 if sv_s > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_k1w (streaming partition: classify + compact + farthest point)",
-                "bytes_per_launch": k1_bytes / max(prof["k1_launches"], 1),
-                "ms_per_launch": prof["k1_ms"] / max(prof["k1_launches"], 1),
-                "timing": "CUDA events around every partition launch, over a second pass of the same K steps "
+                "frac": achieved / peak, "traffic": SIEVE_DRAM_BYTES_PER_POINT * n, "peak_kind": peak_kind,
+                "kernel": "k_sieve (pre-filter + extreme pass: one streaming read of every point)",
+                "bytes_per_launch": sv_bytes / sv_launches,
+                "ms_per_launch": prof["k0_ms"] / sv_launches,
+                "timing": "CUDA events around every sieve launch, over a second pass of the same K steps "
                           f"({ms_prof / args.steps:.3f} ms per step with the events, "
                           f"{ms / args.steps:.3f} ms without)"}
-
-    # the extreme pass against the same peak: 16 bytes read per point
-    k0_bytes = 16.0 * 2 * n * args.steps
-    k0_s = prof["k0_ms"] / 1e3
+    # the partition kernel (all levels) against the same peak: 20 bytes per
+    # point read and per point kept
+    k1_bytes = 20.0 * (prof["k1_points_read"] + prof["k1_points_kept"])
+    k1_s = prof["k1_ms"] / 1e3
     roofline["other_kernels"] = {
-        "k_k0 + k_k0_finalize (extreme pass)": {
-            "achieved": k0_bytes / k0_s / 1e9 if k0_s > 0 else 0.0, "unit": "GB/s",
-            "frac": (k0_bytes / k0_s / 1e9) / peak if k0_s > 0 else 0.0,
-            "ms_per_hull": prof["k0_ms"] / max(prof["calls"], 1)}}
+        "k_k1w (partition, all levels)": {
+            "achieved": k1_bytes / k1_s / 1e9 if k1_s > 0 else 0.0, "unit": "GB/s",
+            "frac": (k1_bytes / k1_s / 1e9) / peak if k1_s > 0 else 0.0,
+            "launches": int(prof["k1_launches"]), "ms_per_hull": prof["k1_ms"] / max(prof["calls"], 1)}}
+    # the whole hull: DRAM bytes per hull (ncu, all kernels) over the device
+    # time per hull of the value's timed region
+    hull_ms = ms_max / args.steps / 2
+    e2e_bytes = sum(HULL_DRAM_BYTES_PER_POINT[d] * n for d in ("square", "disk")) / 2
+    roofline["e2e_frac"] = {
+        "value": e2e_bytes / (hull_ms / 1e3) / 1e9 / peak, "dram_bytes_per_hull": e2e_bytes,
+        "ms_per_hull": hull_ms,
+        "how": "DRAM bytes of every kernel of one hull (ncu dram__bytes_read.sum + dram__bytes_write.sum at "
+               "2e7 points, per point, scaled to the hull's points) over the device time per hull of the "
+               "value's timed region, against the measured HBM peak"}
+
+    # every configuration of the workload list: ms per hull (median of
+    # CUDA-event timed calls), Gpoints/s and the implementation model's bytes
+    configs = None
+    if not args.no_configs and n == FULL_N:
+        configs = bench_configs(vq, torch, stream, dev, survivors, peak)
 
     # end to end through the host-buffer entry point (pinned memory)
     e2e = None
@@ -617,14 +683,14 @@ def main():
             "config": {"workload": WORKLOAD, "points_per_hull": n, "hulls_per_step": 2,
                        "l2": "no flush: each input (1.6 GB at 1e8 points) exceeds L2",
                        "parallelism": f"replicas x{ws}", "hull_sizes": hull_sizes},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "configs": configs,
             "batched": batched, "serving": serving, "energy": energy,
             "gpu_launches": int(prof["launches"]), "clocks": clk,
             "tuning": {"points_per_lane": int(vq.vq_get_config().points_per_thread),
                        "small_max": int(vq.vq_get_config().small_max),
-                       "prefilter": int(vq.vq_get_config().prefilter), "autotune": tuned},
-            "detail": {"profile": prof,
-                       "paper_model_GBps": (8.0 * 2 * n * args.steps + k1_bytes) / (ms_max / 1e3) / 1e9},
+                       "prefilter": int(vq.vq_get_config().prefilter),
+                       "k1_shape": int(vq.vq_get_config().k1_shape), "autotune": tuned},
+            "detail": {"profile": prof, "survivors_per_hull": survivors},
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -134,6 +134,19 @@ vq_status vq_hull2d_host(const double* x_host, const double* y_host, int64_t n, 
 vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t n, int32_t* hull_idx, int64_t* h,
                             void* stream);
 
+/*
+ * Test access to the first (FP32) tier of the exact left-of test of Sec. 2.1:
+ * for m triples tri[6k .. 6k+5] = (ax, ay, bx, by, ux, uy) (device FP64),
+ * d[k] and e[k] (device FP32) receive the value and error bound with which
+ * every kernel of this library evaluates orient(a, b, u) =
+ * (bx-ax)(uy-ay) - (by-ay)(ux-ax) in that tier: a and b as an FP32 line
+ * (truncated origin, rounded direction), u truncated to 24 bits.  The tier
+ * is used only when every |coordinate| < 2^40, and it claims a sign only
+ * when |d| > e; |d - orient| <= e must hold for such inputs.  Synchronises
+ * `stream`.  Returns VQ_ERR_INVALID_ARG for m < 0 or null arrays.
+ */
+vq_status vq_debug_orient_f32(const double* tri, int64_t m, float* d, float* e, void* stream);
+
 /* Tuning knobs (process-wide; take effect on the next call). */
 typedef struct {
   int32_t points_per_thread; /* partition kernel: 4, 8 or 16 points per lane
@@ -164,6 +177,10 @@ typedef struct {
                                 Sec. 6); the hull is the same, the per-level
                                 counters are not.  0: plain Alg. 1 counts.
                                 Applies to the default partition kernel.    */
+  int32_t k1_shape;          /* streaming partition kernel's block shape:
+                                0 (default) 4 warps per block; 1: 8 warps,
+                                a shallower ring; 2: 2 warps, a deeper ring
+                                (per points_per_thread; 0..2)                */
 } vq_config;
 
 vq_status vq_get_config(vq_config* cfg);
@@ -190,7 +207,7 @@ typedef struct {
   int64_t k1_points_read;    /* points classified by the partition kernel     */
   int64_t k1_points_kept;    /* of those, points written to a child           */
   double k0_ms;              /* extreme-point pass (with the pre-filter: the
-                                sieve and the per-set finalize)              */
+                                sieve); the per-set finalize is in other_ms  */
   double k1_ms;              /* partition kernel                              */
   double k2_ms;              /* per-segment finalize                          */
   double k3_ms;              /* small-segment finisher                        */
@@ -206,7 +223,9 @@ vq_status vq_profile_read(vq_profile* out, int32_t reset);
  * Autotuner of the knobs above for inputs like (x, y, n) (device FP64 SoA,
  * as for vq_hull2d).  It times the hull of these points on `stream` under
  * each candidate configuration: points per lane 8 or 16, small-segment
- * threshold 256 or 1024, level-0 pre-filter on or off.  Every candidate runs
+ * threshold 256 or 1024, level-0 pre-filter on or off, and the partition
+ * kernel's three block shapes (warps per block and ring depth), 24
+ * candidates.  Every candidate runs
  * once untimed (workspace, graph capture), then `reps` times (1..16) between
  * CUDA events.  The fastest by its median time becomes the process-wide
  * configuration; the other fields keep their current values.

@@ -81,6 +81,9 @@ def _load():
     lib.orc_verify.restype = ctypes.c_int
     lib.orc_farthest.argtypes = [dp, dp, ctypes.c_int32, ctypes.c_int32, i32p, i64]
     lib.orc_farthest.restype = ctypes.c_int32
+    lib.orc_orient_bound_check.argtypes = [dp, i64, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(i64)]
+    lib.orc_orient_bound_check.restype = i64
     lib.orc_stats_size.restype = i64
     assert lib.orc_stats_size() == ctypes.sizeof(Stats)
     _lib = lib
@@ -124,6 +127,22 @@ def farthest(x, y, a: int, b: int, cand) -> int:
     x, y = _f64(x), _f64(y)
     c = np.ascontiguousarray(cand, dtype=np.int32)
     return int(lib.orc_farthest(_dp(x), _dp(y), int(a), int(b), _ip(c), c.shape[0]))
+
+
+def orient_bound_check(tri, d, e) -> tuple[int, int]:
+    """For triples tri[k] = (ax, ay, bx, by, cx, cy) and approximations d[k]
+    with bounds e[k] of orient(a,b,c) (Sec. 2.1 left-of test): the number
+    of k whose exact orient lies outside [d - e, d + e], and the number with
+    |d| > e whose sign is wrong.  Exact sums of products."""
+    t = np.ascontiguousarray(tri, dtype=np.float64).reshape(-1, 6)
+    dd = np.ascontiguousarray(d, dtype=np.float32)
+    ee = np.ascontiguousarray(e, dtype=np.float32)
+    assert dd.shape[0] == ee.shape[0] == t.shape[0]
+    bad = ctypes.c_int64(0)
+    fp = ctypes.POINTER(ctypes.c_float)
+    out = _load().orc_orient_bound_check(_dp(t), t.shape[0], dd.ctypes.data_as(fp), ee.ctypes.data_as(fp),
+                                         ctypes.byref(bad))
+    return int(out), int(bad.value)
 
 
 def set_filter(on: bool) -> None:

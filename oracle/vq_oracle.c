@@ -186,6 +186,35 @@ int orc_dot_sign(double p0x, double p0y, double p1x, double p1y,
     return orc_sum_products_sign(8, a, b, sg);
 }
 
+/* Checker of an approximate orient with an error bound (used by the tests
+ * of the device's FP32 tier): for m triples tri[6k .. 6k+5] = (ax, ay, bx,
+ * by, cx, cy), counts the k whose exact orient(a,b,c) (the left-of test of
+ * Sec. 2.1) lies outside [d[k] - e[k], d[k] + e[k]], and in *sign_bad the k
+ * with |d[k]| > e[k] whose sign differs from the exact sign.  Both tests
+ * are exact sums of products: orient - d + e >= 0 and d + e - orient >= 0. */
+int64_t orc_orient_bound_check(const double *tri, int64_t m, const float *d, const float *e, int64_t *sign_bad)
+{
+    int64_t out = 0, bad = 0;
+    for (int64_t k = 0; k < m; k++) {
+        const double *t = tri + 6 * k;
+        const double ax = t[0], ay = t[1], bx = t[2], by = t[3], cx = t[4], cy = t[5];
+        const double dk = d[k], ek = e[k];
+        /* orient = bx*cy - bx*ay - ax*cy - by*cx + by*ax + ay*cx */
+        const double a[8] = {bx, bx, ax, by, by, ay, dk, ek};
+        const double b[8] = {cy, ay, cy, cx, ax, cx, 1.0, 1.0};
+        const int lo[8] = {+1, -1, -1, -1, +1, +1, -1, +1}; /* orient - d + e */
+        const int hi[8] = {-1, +1, +1, +1, -1, -1, +1, +1}; /* d + e - orient */
+        if (orc_sum_products_sign(8, a, b, lo) < 0 || orc_sum_products_sign(8, a, b, hi) < 0) out++;
+        if (fabs(dk) > ek) {
+            const int s = orc_sum_products_sign(6, a, b, lo);
+            const int want = dk > 0 ? 1 : -1;
+            if (s != want) bad++;
+        }
+    }
+    if (sign_bad) *sign_bad = bad;
+    return out;
+}
+
 void orc_set_filter(int on) { orc_use_filter = on ? 1 : 0; }
 long long orc_exact_count(void) { return orc_exact_calls; }
 

@@ -28,6 +28,7 @@ struct Config {
   int drop_tile = -1;
   int host_loop = 0;
   int prefilter = 1;
+  int k1_shape = 0;
 };
 
 static std::mutex g_cfg_mu;
@@ -391,6 +392,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   w.timeout_ns = cfg.timeout_ns;
   w.drop_tile = cfg.drop_tile;
   w.ordered = cfg.ordered;
+  w.k1_shape = cfg.k1_shape;
   c.d_stats = w.stats;
 
   const long long launches0 = kernels_launched();
@@ -419,8 +421,8 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   } else {
     VQ_CHECK(launch_k0(w, c.sms * 2, st));  // resident blocks only (2 per SM); tiles of kK0Tile points
   }
-  VQ_CHECK(launch_k0_finalize(w, st));
   VQ_CHECK(tm.end());
+  VQ_TIMED(tm, kKindOther, launch_k0_finalize(w, st));
   VQ_TIMED(tm, kKindOther, launch_tilemap(w, 0, c.sms * 4, st));
 
   int level = 0;
@@ -884,11 +886,13 @@ vq_status vq_autotune(const double* x, const double* y, int64_t n, int32_t reps,
   const int ppts[2] = {8, 16}, smalls[2] = {256, 1024}, pres[2] = {0, 1};
   for (int a = 0; a < 2 && result == VQ_OK; a++)
     for (int b = 0; b < 2 && result == VQ_OK; b++)
-      for (int d = 0; d < 2 && result == VQ_OK; d++) {
+      for (int d = 0; d < 2 && result == VQ_OK; d++)
+        for (int k = 0; k < 3 && result == VQ_OK; k++) {
         Config cand = base;
         cand.ppt = ppts[a];
         cand.small_max = smalls[b];
         cand.prefilter = pres[d];
+        cand.k1_shape = k;
         cand.profile = 0;
         cand.ordered = 0;
         {
@@ -955,6 +959,7 @@ vq_status vq_get_config(vq_config* cfg) {
   cfg->ordered = c.ordered;
   cfg->host_loop = c.host_loop;
   cfg->prefilter = c.prefilter;
+  cfg->k1_shape = c.k1_shape;
   return VQ_OK;
 }
 
@@ -965,6 +970,7 @@ vq_status vq_set_config(const vq_config* cfg) {
   if (cfg->small_max < 2 || cfg->small_max > kK3Cap) return VQ_ERR_INVALID_ARG;
   if (cfg->k1_blocks_per_sm < 0 || cfg->k1_blocks_per_sm > 32) return VQ_ERR_INVALID_ARG;
   if (cfg->timeout_ns <= 0) return VQ_ERR_INVALID_ARG;
+  if (cfg->k1_shape < 0 || cfg->k1_shape > 2) return VQ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(g_cfg_mu);
   g_cfg.ppt = cfg->points_per_thread;
   g_cfg.small_max = cfg->small_max;
@@ -975,6 +981,15 @@ vq_status vq_set_config(const vq_config* cfg) {
   g_cfg.ordered = cfg->ordered ? 1 : 0;
   g_cfg.host_loop = cfg->host_loop ? 1 : 0;
   g_cfg.prefilter = cfg->prefilter ? 1 : 0;
+  g_cfg.k1_shape = cfg->k1_shape;
+  return VQ_OK;
+}
+
+vq_status vq_debug_orient_f32(const double* tri, int64_t m, float* d, float* e, void* stream) {
+  if (m < 0 || (m > 0 && (!tri || !d || !e))) return VQ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  VQ_CHECK(launch_debug_orient_f32(tri, m, d, e, st));
+  VQ_CHECK(cudaStreamSynchronize(st));
   return VQ_OK;
 }
 

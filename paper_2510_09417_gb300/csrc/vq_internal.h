@@ -61,6 +61,7 @@ struct Work {
   int drop_tile;             // test knob: this K1 tile never publishes (-1: none)
   int ordered;               // 1: offsets by decoupled look-back (stable layout); 0: atomic cursors
   int all_fast;              // host's copy of !Ctrl::any_slow: selects the FP32-only partition kernel
+  int k1_shape;              // streaming partition kernel: block shape 0..2 (warps per block, ring stages)
   int tier_dev;              // 1: both partition kernels are launched and the device's Ctrl::any_slow
                              // picks the one that runs (no host round trip); all_fast is then unused
   PolyF* poly;               // per set: pre-filter chains and inner box
@@ -84,6 +85,8 @@ cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, long 
 // level after level 0 has segments (the WHILE node's first test)
 cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphNode_t* node, const Work& w, cudaGraphConditionalHandle h);
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st);
+// the streaming partition kernel (vq_partition.cu), block shape w.k1_shape
+cudaError_t launch_k1w(const Work& w, int level, int ppt, int tiles, cudaStream_t st);
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st);
 cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st);
 cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st);
@@ -93,6 +96,7 @@ cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long 
 // indices back to original indices
 cudaError_t launch_gather(const double* x, const double* y, const int* idx, long long m, long long base, double* mx,
                           double* my, int* mid, cudaStream_t st);
+cudaError_t launch_debug_orient_f32(const double* tri, long long m, float* d, float* e, cudaStream_t st);
 cudaError_t launch_map_indices(const int* mout, const int* mid, long long h, int* out, cudaStream_t st);
 cudaError_t scan_exclusive_i32(int* data, long long n, int* tmp, cudaStream_t st);
 cudaError_t scan_exclusive_i64(long long* data, long long n, long long* tmp, cudaStream_t st);

@@ -29,6 +29,7 @@
 #include <climits>
 
 #include "vq_internal.h"
+#include "vq_common.cuh"
 
 namespace vq {
 
@@ -39,24 +40,6 @@ long long kernels_launched() { return (long long)__atomic_load_n(&g_launches, __
 // ---------------------------------------------------------------------------
 // shared helpers
 // ---------------------------------------------------------------------------
-
-// Checked builds (VQ_CHECKED=1) validate computed indices before use: a
-// failure records its site and value, raises kErrInternal and skips the access.
-#ifdef VQ_CHECKED
-#define VQ_OK_IDX(w, site, v, lo, hi) vq_check_idx((w), (site), (long long)(v), (long long)(lo), (long long)(hi))
-__device__ __forceinline__ bool vq_check_idx(const Work& w, int site, long long v, long long lo, long long hi) {
-  if (v >= lo && v < hi) return true;
-  if (atomicCAS(&w.ctrl->dbg_site, 0, site) == 0) w.ctrl->dbg_val = v;
-  atomicOr(&w.ctrl->err, kErrInternal);
-  return false;
-}
-#else
-#define VQ_OK_IDX(w, site, v, lo, hi) true
-#endif
-
-__device__ __forceinline__ bool fatal(const Work& w) {
-  return (*reinterpret_cast<volatile unsigned*>(&w.ctrl->err) & kErrFatal) != 0;
-}
 
 __device__ __forceinline__ void emit(const Work& w, long long key, int local) {
   if (!VQ_OK_IDX(w, 1, key, 0, w.nkeys) || !VQ_OK_IDX(w, 2, local, 0, w.N)) return;
@@ -520,45 +503,6 @@ __global__ void k_level_cond(Work w, cudaGraphConditionalHandle h, long long max
 // K1: fused classify + compact + per-tile argmax
 // ---------------------------------------------------------------------------
 
-// Running exact argmax of one thread: replace the best when the new point
-// beats it (bounds first, exact tiers only when the bounds overlap).
-template <typename K>
-__device__ __forceinline__ void take_best(CandT<K>& b, const double* L, double x, double y, int idx, K key, K err) {
-  const K lo = key_lo(key, err), hi = key_hi(key, err);
-  if (b.idx >= 0 && hi < b.lo) return;  // clearly nearer the line
-  if (b.idx < 0 || lo > b.hi || beats_exact(L[0], L[1], L[2], L[3], x, y, idx, b.x, b.y, b.idx)) {
-    b.x = x; b.y = y; b.lo = lo; b.hi = hi; b.idx = idx;
-  }
-}
-
-template <typename K>
-__device__ __forceinline__ CandT<double> to_double(const CandT<K>& c) {
-  CandT<double> d;
-  d.x = c.x; d.y = c.y; d.lo = widen(c.lo); d.hi = widen(c.hi); d.idx = c.idx;
-  return d;
-}
-
-__device__ __forceinline__ BestRec to_rec(const CandT<double>& c) {
-  BestRec r;
-  r.x = c.x; r.y = c.y; r.lo = c.lo; r.hi = c.hi; r.idx = c.idx; r.pad = 0;
-  return r;
-}
-__device__ __forceinline__ CandT<double> from_rec(const BestRec& r) {
-  CandT<double> c;
-  c.x = r.x; c.y = r.y; c.lo = r.lo; c.hi = r.hi; c.idx = r.idx;
-  return c;
-}
-__device__ __forceinline__ BestRec load_rec(const BestRec* p) {
-  BestRec r;
-  r.x = __ldcg(&p->x);
-  r.y = __ldcg(&p->y);
-  r.lo = __ldcg(&p->lo);
-  r.hi = __ldcg(&p->hi);
-  r.idx = __ldcg(&p->idx);
-  r.pad = 0;
-  return r;
-}
-
 // Decoupled look-back (Merrill and Garland, "Single-pass Parallel Prefix
 // Scan with Decoupled Look-back", 2016), restarted at every segment, carrying
 // two sums (left and right child counts) and two running maxima (the
@@ -681,9 +625,6 @@ __device__ __forceinline__ void tile_atomic(const Work& w, int par, int sid, int
 }
 
 // ---- asynchronous global -> shared copies (cp.async, per thread) ----
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
@@ -946,7 +887,6 @@ __global__ void __launch_bounds__(kK1Threads) k_k1(Work w, int level) {
   }
 }
 
-#include "vq_partition.cuh"
 #include "vq_sieve.cuh"
 
 // ---------------------------------------------------------------------------
@@ -1527,7 +1467,17 @@ cudaError_t launch_seed(const Work& w, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-static int device_sms();
+static int device_sms() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (sms[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+    sms[dev] = n;
+  }
+  return sms[dev];
+}
 
 // upper bound of the extreme-pass tiles (exact for one set)
 static long long k0_tiles_bound(const Work& w) {
@@ -1676,90 +1626,8 @@ static cudaError_t launch_k1_ppt(const Work& w, int level, int grid, cudaStream_
   return cudaLaunchKernelEx(&cfg, k_k1<PPT, false>, w, level);
 }
 
-// Streaming partition kernel (vq_partition.cuh): independent warps, each
-// with a ring of NS stages of 32 * ppt points; WPB warps per block.
-template <int PPT>
-struct K1WCfg;
-template <>
-struct K1WCfg<4> { static constexpr int WPB = 4, NS = 4; };
-template <>
-struct K1WCfg<8> { static constexpr int WPB = 4, NS = 3; };
-template <>
-struct K1WCfg<16> { static constexpr int WPB = 4, NS = 2; };
-
-static int device_sms() {
-  static int sms[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-  if (sms[dev] == 0) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
-    sms[dev] = n;
-  }
-  return sms[dev];
-}
-
-template <int PPT, bool ALLFAST>
-static int k1w_blocks_per_sm() {
-  constexpr int WPB = K1WCfg<PPT>::WPB, NS = K1WCfg<PPT>::NS;
-  typedef K1W<PPT, WPB, NS> C;
-  static int occ[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
-  if (occ[dev] > 0) return occ[dev];
-  if (cudaFuncSetAttribute(k_k1w<PPT, WPB, NS, true, ALLFAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)C::smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_k1w<PPT, WPB, NS, false, ALLFAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)C::smem) != cudaSuccess)
-    return -1;
-  int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_k1w<PPT, WPB, NS, true, ALLFAST>, 32 * WPB, C::smem) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_k1w<PPT, WPB, NS, false, ALLFAST>, 32 * WPB, C::smem) !=
-          cudaSuccess)
-    return -1;
-  const int n = a < b ? a : b;
-  occ[dev] = n > 0 ? n : 1;
-  return occ[dev];
-}
-
-template <int PPT, bool ALLFAST>
-static cudaError_t launch_k1w_ppt(const Work& w, int level, int tiles, cudaStream_t st) {
-  constexpr int WPB = K1WCfg<PPT>::WPB, NS = K1WCfg<PPT>::NS;
-  typedef K1W<PPT, WPB, NS> C;
-  if (w.tile != C::TW) return cudaErrorInvalidValue;
-  const int occ = k1w_blocks_per_sm<PPT, ALLFAST>();
-  if (occ < 0) return cudaErrorInvalidConfiguration;
-  long long grid = (long long)occ * device_sms();
-  const long long need = ((long long)tiles + WPB - 1) / WPB;
-  if (grid > need) grid = need;
-  if (grid < 1) grid = 1;
-  count_launch();
-  if (level == 0 && !w.sieve)
-    k_k1w<PPT, WPB, NS, true, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
-  else
-    k_k1w<PPT, WPB, NS, false, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
-  return cudaGetLastError();
-}
-
-template <int PPT>
-static cudaError_t launch_k1w_sel(const Work& w, int level, int tiles, cudaStream_t st) {
-  if (w.tier_dev) {  // both; the device's flag lets one of them work
-    const cudaError_t e = launch_k1w_ppt<PPT, true>(w, level, tiles, st);
-    return e != cudaSuccess ? e : launch_k1w_ppt<PPT, false>(w, level, tiles, st);
-  }
-  return w.all_fast ? launch_k1w_ppt<PPT, true>(w, level, tiles, st) : launch_k1w_ppt<PPT, false>(w, level, tiles, st);
-}
-
 cudaError_t launch_k1(const Work& w, int level, int ppt, int grid, cudaStream_t st) {
-  if (!w.ordered) {
-    switch (ppt) {
-      case 4: return launch_k1w_sel<4>(w, level, grid, st);
-      case 8: return launch_k1w_sel<8>(w, level, grid, st);
-      case 16: return launch_k1w_sel<16>(w, level, grid, st);
-      default: return cudaErrorInvalidValue;
-    }
-  }
+  if (!w.ordered) return launch_k1w(w, level, ppt, grid, st);  // vq_partition.cu
   switch (ppt) {
     case 4: return launch_k1_ppt<4>(w, level, grid, st);
     case 8: return launch_k1_ppt<8>(w, level, grid, st);
@@ -1790,6 +1658,30 @@ int k1_blocks_per_sm(int ppt) {
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st) {
   count_launch();
   k_k2<<<grid, 256, 0, st>>>(w, level);
+  return cudaGetLastError();
+}
+
+// Test access to the FP32 tier: for triples (ax, ay, bx, by, ux, uy) the
+// evaluation of orient(a, b, u) that the partition, finalize and pre-filter
+// kernels use: make_line on the exact endpoints, trunc_f32 of the point,
+// orient_f32 with its bound.
+__global__ void k_debug_orient_f32(const double* tri, long long m, float* d, float* e) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x) {
+    const double* t = tri + 6 * k;
+    const LineF L = make_line(t[0], t[1], t[2], t[3]);
+    float key, err;
+    line_key_k(L, nullptr, t[4], t[5], key, err);
+    d[k] = key;
+    e[k] = err;
+  }
+}
+
+cudaError_t launch_debug_orient_f32(const double* tri, long long m, float* d, float* e, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  long long blocks = (m + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  count_launch();
+  k_debug_orient_f32<<<(unsigned)blocks, 256, 0, st>>>(tri, m, d, e);
   return cudaGetLastError();
 }
 

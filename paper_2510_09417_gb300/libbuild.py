@@ -15,8 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libvqhull.so")
 STAMP = os.path.join(BUILD, "lib.arch")
-SOURCES = ["vq_kernels.cu", "vq_api.cu", "vq_server.cu", "vq_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, h) for h in ("vq_device.cuh", "vq_internal.h", "vq_partition.cuh", "vq_admit.h")] + [
+SOURCES = ["vq_kernels.cu", "vq_partition.cu", "vq_api.cu", "vq_server.cu", "vq_noalloc.cu"]
+HEADERS = [os.path.join(CSRC, h) for h in ("vq_device.cuh", "vq_internal.h", "vq_common.cuh", "vq_partition.cuh",
+                                            "vq_sieve.cuh", "vq_admit.h")] + [
     os.path.join(ROOT, "include", "vqhull.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

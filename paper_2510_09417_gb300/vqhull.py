@@ -40,6 +40,7 @@ class Config(ctypes.Structure):
         ("ordered", ctypes.c_int32),
         ("host_loop", ctypes.c_int32),
         ("prefilter", ctypes.c_int32),
+        ("k1_shape", ctypes.c_int32),
     ]
 
 
@@ -84,7 +85,8 @@ class ServerInfo(ctypes.Structure):
 
 SYMBOLS = (
     "vq_status_string", "vq_version", "vq_hull2d", "vq_hull2d_batched", "vq_hull2d_host", "vq_hull2d_noalloc",
-    "vq_get_config", "vq_set_config", "vq_last_stats", "vq_profile_read", "vq_autotune", "vq_server_create", "vq_server_submit",
+    "vq_get_config", "vq_set_config", "vq_last_stats", "vq_profile_read", "vq_autotune", "vq_debug_orient_f32",
+    "vq_server_create", "vq_server_submit",
     "vq_server_poll", "vq_server_wait", "vq_server_wait_any", "vq_server_stats", "vq_server_info_read", "vq_server_destroy",
 )
 
@@ -128,6 +130,8 @@ def load(build_if_missing: bool = True):
         lib.vq_profile_read.restype = ctypes.c_int
         lib.vq_autotune.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_double), vp]
         lib.vq_autotune.restype = ctypes.c_int
+        lib.vq_debug_orient_f32.argtypes = [vp, i64, vp, vp, vp]
+        lib.vq_debug_orient_f32.restype = ctypes.c_int
         lib.vq_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
         lib.vq_server_create.restype = ctypes.c_int
         lib.vq_server_submit.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
@@ -268,6 +272,21 @@ def vq_set_config(cfg: Config | None = None, **kw) -> Config:
         setattr(c, k, v)
     _check(load().vq_set_config(ctypes.byref(c)), "vq_set_config")
     return c
+
+
+def vq_debug_orient_f32(tri: torch.Tensor, stream=None):
+    """The FP32 tier's value and bound of orient(a, b, u) for device FP64
+    triples tri[k] = (ax, ay, bx, by, ux, uy): returns (d, e) on the device."""
+    lib = load()
+    if not isinstance(tri, torch.Tensor) or tri.device.type != "cuda" or tri.dtype != torch.float64:
+        raise TypeError("tri must be a CUDA float64 tensor")
+    t = tri.contiguous().reshape(-1, 6)
+    m = t.shape[0]
+    d = torch.empty(m, dtype=torch.float32, device=t.device)
+    e = torch.empty(m, dtype=torch.float32, device=t.device)
+    _check(lib.vq_debug_orient_f32(t.data_ptr(), m, d.data_ptr(), e.data_ptr(), _stream_ptr(stream)),
+           "vq_debug_orient_f32")
+    return d, e
 
 
 def vq_autotune(x: torch.Tensor, y: torch.Tensor, reps: int = 3, stream=None):

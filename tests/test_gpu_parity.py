@@ -119,7 +119,7 @@ def test_full_size_1e8(vq, dist):
     got = gpu_hull(vq, x, y)
     code, bad = oracle.verify(x, y, got)
     assert code == 0, (oracle.VERIFY_CODES.get(code), bad)
-    if dist in ("square", "kuzmin"):
+    if dist in ("square", "kuzmin", "disk"):
         assert np.array_equal(got, oracle.hull(x, y))
 
 

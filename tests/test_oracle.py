@@ -71,6 +71,47 @@ def test_orient_sign_matches_integer_arithmetic(use_filter):
     assert oracle._load().orc_exact_count() > before  # and the exact path ran
 
 
+def test_orient_bound_check():
+    """The checker of approximate orients with bounds (used to pin the
+    device's FP32 tier) against exact rational arithmetic: each interval
+    [d - e, d + e] is classified by Fractions, and the wrong-sign count by
+    the exact sign."""
+    from fractions import Fraction
+    rng = np.random.default_rng(23)
+    tri, dd, ee, want_out, want_bad = [], [], [], 0, 0
+    for a, b, c in _near_degenerate_triples(rng, 4000):
+        if max(abs(v) for v in a + b + c) > 2.0 ** 40 or max(abs(v) for v in a + b + c if v) < 2.0 ** -40:
+            continue
+        fa = [Fraction(v) for v in a + b + c]
+        exact = (fa[2] - fa[0]) * (fa[5] - fa[1]) - (fa[3] - fa[1]) * (fa[4] - fa[0])
+        d = np.float32(float(exact))
+        err = abs(Fraction(float(d)) - exact)
+        mode = rng.integers(0, 4)
+        if mode == 0:    # a bound that just covers the error
+            e = np.float32(float(err))
+            while Fraction(float(e)) < err:
+                e = np.nextafter(e, np.float32(np.inf))
+        elif mode == 1:  # a bound that just misses it (when there is an error)
+            e = np.float32(float(err))
+            while Fraction(float(e)) >= err and e > 0:
+                e = np.nextafter(e, np.float32(0))
+        elif mode == 2:  # the sign flipped with a tight bound
+            d = np.float32(-d)
+            e = np.float32(0.0)
+        else:            # a wide bound
+            e = np.float32(abs(float(d)) * 4 + 1.0)
+        lo, hi = Fraction(float(d)) - Fraction(float(e)), Fraction(float(d)) + Fraction(float(e))
+        want_out += not (lo <= exact <= hi)
+        if abs(float(d)) > float(e):
+            want_bad += (1 if float(d) > 0 else -1) != (exact > 0) - (exact < 0)
+        tri.append(a + b + c)
+        dd.append(d)
+        ee.append(e)
+    out, bad = oracle.orient_bound_check(np.array(tri), np.array(dd, dtype=np.float32), np.array(ee, dtype=np.float32))
+    assert len(tri) > 1000 and want_out > 100 and want_bad > 100
+    assert (out, bad) == (want_out, want_bad)
+
+
 @pytest.mark.parametrize("use_filter", [True, False])
 def test_cross_and_dot_signs(use_filter):
     oracle.set_filter(use_filter)
