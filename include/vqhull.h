@@ -135,17 +135,21 @@ vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t n, int32_t
                             void* stream);
 
 /*
- * Test access to the first (FP32) tier of the exact left-of test of Sec. 2.1:
- * for m triples tri[6k .. 6k+5] = (ax, ay, bx, by, ux, uy) (device FP64),
- * d[k] and e[k] (device FP32) receive the value and error bound with which
- * every kernel of this library evaluates orient(a, b, u) =
- * (bx-ax)(uy-ay) - (by-ay)(ux-ax) in that tier: a and b as an FP32 line
- * (truncated origin, rounded direction), u truncated to 24 bits.  The tier
- * is used only when every |coordinate| < 2^40, and it claims a sign only
- * when |d| > e; |d - orient| <= e must hold for such inputs.  Synchronises
- * `stream`.  Returns VQ_ERR_INVALID_ARG for m < 0 or null arrays.
+ * Test access to the FP32 tiers of the exact left-of test of Sec. 2.1: for
+ * m triples tri[6k .. 6k+5] = (ax, ay, bx, by, ux, uy) (device FP64), d[k]
+ * and e[k] (device FP32) receive the value and error bound with which every
+ * kernel of this library evaluates orient(a, b, u) =
+ * (bx-ax)(uy-ay) - (by-ay)(ux-ax) in that tier:
+ *   tier 0  a and b as an FP32 line (truncated origin, rounded direction),
+ *           u truncated to 24 bits (absolute coordinates);
+ *   tier 1  the same direction, u - a computed in FP64 and rounded to FP32
+ *           (coordinates relative to a), for near-collinear points.
+ * The tiers are used only when every |coordinate| < 2^40, and they claim a
+ * sign only when |d| > e; |d - orient| <= e must hold for such inputs.
+ * Synchronises `stream`.  Returns VQ_ERR_INVALID_ARG for m < 0, null arrays
+ * or another tier.
  */
-vq_status vq_debug_orient_f32(const double* tri, int64_t m, float* d, float* e, void* stream);
+vq_status vq_debug_orient_f32(const double* tri, int64_t m, int32_t tier, float* d, float* e, void* stream);
 
 /* Tuning knobs (process-wide; take effect on the next call). */
 typedef struct {

@@ -985,10 +985,10 @@ vq_status vq_set_config(const vq_config* cfg) {
   return VQ_OK;
 }
 
-vq_status vq_debug_orient_f32(const double* tri, int64_t m, float* d, float* e, void* stream) {
-  if (m < 0 || (m > 0 && (!tri || !d || !e))) return VQ_ERR_INVALID_ARG;
+vq_status vq_debug_orient_f32(const double* tri, int64_t m, int32_t tier, float* d, float* e, void* stream) {
+  if (m < 0 || (m > 0 && (!tri || !d || !e)) || tier < 0 || tier > 1) return VQ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  VQ_CHECK(launch_debug_orient_f32(tri, m, d, e, st));
+  VQ_CHECK(launch_debug_orient_f32(tri, m, tier, d, e, st));
   VQ_CHECK(cudaStreamSynchronize(st));
   return VQ_OK;
 }

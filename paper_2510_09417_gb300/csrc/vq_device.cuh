@@ -283,6 +283,36 @@ __device__ __forceinline__ void orient_f32(const LineF& L, float ux, float uy, f
 }
 
 // ---------------------------------------------------------------------------
+// Tier 1b: FP32 in coordinates relative to the line's first endpoint o, for
+// points that the absolute tier leaves undecided because they are nearly
+// collinear far from the origin (hull-dense inputs such as points on a
+// circle).  With T = u - o and D = e - o (exact), T~ = fl32(fl64(u - o)),
+// D~ the line's rounded direction (as above), p = fl(D~y T~x) and
+// d~ = fl(D~x T~y - p) (one FMA), writing |T~ - T| <= a |T~| + b and
+// |D~ - D| <= a |D~| + b with a = 2^-24 (1 + 2^-20), b = 2^-148:
+//   |d~ - d| <= 2^-24 |d~| + (2a (1 + a) + 2^-24) (|D~x||T~y| + |D~y||T~x|)
+//               + b (1 + a) (|D~x| + |D~y| + |T~x| + |T~y|) + 2^-149,
+// and with rho = max |D~| (|D~x||T~y| + |D~y||T~x| <= rho m, m = |T~x| + |T~y|)
+// this is covered by E = 2^-22 |d~| + (k + 2^-146) m + (k 2^-110 + 2^-140),
+// k = 4 * 2^-23 rho (1 + 2^-21) the absolute tier's constant, evaluated with
+// upward rounding: no term depends on the magnitude of o or u.  Valid for
+// all |coordinates| < 2^40 (nothing overflows FP32); the two FP64
+// subtractions are the tier's only FP64 work.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void orient_rel(const LineF& L, double ox, double oy, double ux, double uy, float& d,
+                                           float& e) {
+  const float tx = __double2float_rn(__dsub_rn(ux, ox));
+  const float ty = __double2float_rn(__dsub_rn(uy, oy));
+  const float m = __fadd_ru(fabsf(tx), fabsf(ty));
+  const float p = __fmul_rn(L.dy, tx);
+  d = __fmaf_rn(L.dx, ty, -p);
+  const float k = __fadd_ru(L.k, 0x1p-146f);
+  const float c = __fmaf_ru(L.k, 0x1p-110f, 0x1p-140f);
+  e = __fmaf_ru(fabsf(d), 0x1p-22f, __fmaf_ru(k, m, c));
+}
+
+// ---------------------------------------------------------------------------
 // Tier 2: FP64 with separately rounded operations (never contracted).
 // ---------------------------------------------------------------------------
 
@@ -724,6 +754,45 @@ __device__ __forceinline__ void line_key_k(const LineF&, const double* E, double
                                            double& err) {
   bool sure;
   cross_f64(E[0], E[1], E[2], E[3], E[0], E[1], ux, uy, key, err, sure);
+}
+
+// The tighter of the FP32 evaluations: the absolute tier, and when its
+// bound is wide next to the value (near-collinear points), the relative
+// tier (both bound the same exact value).  The FP64 variant is line_key_k.
+__device__ __forceinline__ void line_key_tight(const LineF& L, const double* E, double ux, double uy, float& key,
+                                               float& err) {
+  line_key_k(L, E, ux, uy, key, err);
+  if (err > 0x1p-8f * fabsf(key)) {
+    float k2, e2;
+    orient_rel(L, E[0], E[1], ux, uy, k2, e2);
+    if (e2 < err) {
+      key = k2;
+      err = e2;
+    }
+  }
+}
+__device__ __forceinline__ void line_key_tight(const LineF& L, const double* E, double ux, double uy, double& key,
+                                               double& err) {
+  line_key_k(L, E, ux, uy, key, err);
+}
+
+// Classification by the relative tier (for points the absolute tier left
+// undecided): 0, 1, 2 as classify_filter, 3 when it is unsure as well.
+__device__ __forceinline__ int classify_rel(const SegGeom& g, const LineF& l1, const LineF& l2, double ux,
+                                            double uy, float& key, float& err) {
+  float d1, e1;
+  orient_rel(l1, g.ax, g.ay, ux, uy, d1, e1);
+  if (d1 > e1) { key = d1; err = e1; return 1; }
+  if (!(d1 < -e1)) return 3;
+  float d2, e2;
+  orient_rel(l2, g.rx, g.ry, ux, uy, d2, e2);
+  if (d2 > e2) { key = d2; err = e2; return 2; }
+  if (!(d2 < -e2)) return 3;
+  return 0;
+}
+__device__ __forceinline__ int classify_rel(const SegGeom&, const LineF&, const LineF&, double, double, double&,
+                                            double&) {
+  return 3;
 }
 
 }  // namespace vq

@@ -18,10 +18,8 @@ constexpr int kSampleChunk = 4096;  // pre-filter sample: the first kSampleChunk
 constexpr int kSampleEvery = 16;    // kSampleEvery-th extreme-pass tile of a set (1/128 of the points)
 constexpr int kSvWarps = 8;         // sieve: warps per block
 constexpr int kSvMaxBlocks = 4096;  // sieve: most blocks (its partials: one per block and set)
-constexpr int kK3Cap = 1024;        // points per warp in the small-segment kernel
-constexpr int kK3Warps = 4;
-constexpr int kK3Stack = 24;
-constexpr int kK3StatLevels = 64;  // levels whose counters the small-segment kernel sums per warp
+constexpr int kK3Cap = 1024;        // points per segment in the small-segment kernel (one block each)
+constexpr int kK3StatLevels = 64;  // levels whose counters the small-segment kernel sums per block
 constexpr int kK4Words = 1024;      // bitmap words per ordering block (256 threads x 4)
 constexpr int kFillTiles = 1024;    // tiles per tile-map fill job
 
@@ -96,7 +94,7 @@ cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long 
 // indices back to original indices
 cudaError_t launch_gather(const double* x, const double* y, const int* idx, long long m, long long base, double* mx,
                           double* my, int* mid, cudaStream_t st);
-cudaError_t launch_debug_orient_f32(const double* tri, long long m, float* d, float* e, cudaStream_t st);
+cudaError_t launch_debug_orient_f32(const double* tri, long long m, int tier, float* d, float* e, cudaStream_t st);
 cudaError_t launch_map_indices(const int* mout, const int* mid, long long h, int* out, cudaStream_t st);
 cudaError_t scan_exclusive_i32(int* data, long long n, int* tmp, cudaStream_t st);
 cudaError_t scan_exclusive_i64(long long* data, long long n, long long* tmp, cudaStream_t st);

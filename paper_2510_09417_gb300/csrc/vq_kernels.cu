@@ -1017,255 +1017,10 @@ __global__ void k_k2(Work w, int level) {
 }
 
 // ---------------------------------------------------------------------------
-// K3: small segments, one warp each, finished in shared memory
+// K3: small segments, one block each, finished in shared memory
 // ---------------------------------------------------------------------------
 
-struct Frame {
-  double ax, ay, bx, by;  // endpoint coordinates (no global reload per frame)
-  LineF la;               // FP32-tier constants of a->b (from the parent's geometry)
-  int lo, hi;   // range in the warp's permutation buffer
-  int a, b, r;  // global indices; r < 0 until computed
-  int buf;
-  int depth;
-  int pad;
-};
-
-// Exact farthest point of P[lo, hi) from the line E = {ox, oy, ex, ey}
-// (E in shared memory, read only by the exact tiers and the FP64 keys).
-template <bool FAST>
-__device__ CandT<double> small_argmax(const double* X, const double* Y, const int* I, const unsigned short* P,
-                                      int lo, int hi, const double* E, const LineF& L, int lane) {
-  // the largest lower bound first (independent iterations), then exact
-  // comparisons only among the points whose upper bound reaches it
-  typedef typename KeyOf<FAST>::T K;
-  K lmax = key_neg_inf<K>();
-  for (int l = lo + lane; l < hi; l += kWarp) {
-    const int u = P[l];
-    K key, err;
-    line_key_k(L, E, X[u], Y[u], key, err);
-    lmax = key_max(lmax, key_lo(key, err));
-  }
-  const K Lw = warp_max_k(lmax);
-  CandT<K> best = cand_none<K>();
-  for (int l = lo + lane; l < hi; l += kWarp) {
-    const int u = P[l];
-    K key, err;
-    line_key_k(L, E, X[u], Y[u], key, err);
-    if (key_hi(key, err) >= Lw) take_best(best, E, X[u], Y[u], I[u], key, err);
-  }
-  const unsigned lanes = __ballot_sync(kFull, best.idx >= 0);
-  if (__popc(lanes) > 1) best = warp_best(E, best);
-  else if (lanes) best = shfl_xor_cand(best, lane ^ (__ffs(lanes) - 1));
-  return to_double(best);
-}
-
-// One warp finishes a segment of <= kK3Cap points held in shared memory:
-// Alg. 1's recursion with an explicit stack, one partition per step.
-__device__ void small_solve(const Work& w, const SegRec& S, double* X, double* Y, int* I, unsigned short* P0,
-                            unsigned short* P1, Frame* stk, SegGeom* G, double* E, unsigned long long* kst,
-                            int lane) {
-  const bool fast = (S.flags & kSegFast) != 0;
-  const unsigned lt = lanemask_lt();
-  int top = 0;
-  if (lane == 0) {
-    Frame f;
-    f.ax = w.x[S.a]; f.ay = w.y[S.a]; f.bx = w.x[S.b]; f.by = w.y[S.b];
-    f.la = fast ? make_line(f.ax, f.ay, f.bx, f.by) : LineF{};
-    f.lo = 0; f.hi = S.len; f.a = S.a; f.b = S.b; f.r = S.r; f.buf = 0; f.depth = 0; f.pad = 0;
-    stk[0] = f;
-  }
-  top = 1;
-  __syncwarp();
-#ifdef VQ_K1_PROFILE
-  // [0] frames, [1] argmax cycles, [2] geometry cycles, [3] classify cycles,
-  // [4] points classified, [5] points sent to the exact tiers, [6] frame total
-  unsigned long long kp[7] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-#define K3_MARK(v) const unsigned long long v = clock64()
-#else
-#define K3_MARK(v)
-#endif
-  while (top > 0) {
-    K3_MARK(q0);
-    top--;
-    const Frame f = stk[top];
-    __syncwarp();
-    if (!VQ_OK_IDX(w, 12, f.a, 0, w.N) || !VQ_OK_IDX(w, 13, f.b, 0, w.N) ||
-        !VQ_OK_IDX(w, 14, f.hi, f.lo + 1, S.len + 1) || !VQ_OK_IDX(w, 15, f.lo, 0, S.len))
-      return;
-    unsigned short* Pin = f.buf ? P1 : P0;
-    unsigned short* Pout = f.buf ? P0 : P1;
-    if (lane == 0) { E[0] = f.ax; E[1] = f.ay; E[2] = f.bx; E[3] = f.by; }
-    __syncwarp();
-    int r = f.r;
-    double rx = 0.0, ry = 0.0;
-    if (r < 0) {
-      const CandT<double> best = fast ? small_argmax<true>(X, Y, I, Pin, f.lo, f.hi, E, f.la, lane)
-                                      : small_argmax<false>(X, Y, I, Pin, f.lo, f.hi, E, f.la, lane);
-      r = best.idx;
-      rx = best.x;
-      ry = best.y;
-    } else if (lane == 0 && VQ_OK_IDX(w, 16, r, 0, w.N)) {
-      rx = w.x[r];
-      ry = w.y[r];
-    }
-    K3_MARK(q1);
-    if (r < 0) {
-      if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
-      return;
-    }
-    if (!VQ_OK_IDX(w, 16, r, 0, w.N)) return;
-    if (lane == 0) fill_geom(*G, E[0], E[1], E[2], E[3], rx, ry);
-    __syncwarp();
-    K3_MARK(q2);
-    LineF l1 = {}, l2 = {};
-    if (fast) { l1 = line1_of(*G); l2 = line2_of(*G); }
-    int nL = 0, nR = 0;
-    for (int base = f.lo; base < f.hi; base += kWarp) {
-      const int l = base + lane;
-      int c = 0;
-      unsigned short u = 0;
-      if (l < f.hi) {
-        u = Pin[l];
-        if (fast) { float k, e; c = classify_filter(*G, l1, l2, X[u], Y[u], k, e); }
-        else { double k, e; c = classify_filter(*G, l1, l2, X[u], Y[u], k, e); }
-#ifdef VQ_K1_PROFILE
-        kp[4]++;
-        if (c == 3) kp[5]++;
-#endif
-        if (c == 3) c = classify_exact(G, X[u], Y[u]);
-      }
-      const unsigned mL = __ballot_sync(kFull, c == 1), mR = __ballot_sync(kFull, c == 2);
-      if (c == 1) Pout[f.lo + nL + __popc(mL & lt)] = u;
-      if (c == 2) Pout[f.hi - 1 - (nR + __popc(mR & lt))] = u;
-      nL += __popc(mL);
-      nR += __popc(mR);
-    }
-    __syncwarp();
-    K3_MARK(q3);
-#ifdef VQ_K1_PROFILE
-    kp[0]++;
-    kp[1] += q1 - q0;
-    kp[2] += q2 - q1;
-    kp[3] += q3 - q2;
-#endif
-    if (lane == 0) {
-      emit(w, (long long)S.off + f.lo + nL + 1 + S.shift, r - S.set_off);
-      const int lvl = S.level + f.depth;
-      if (lvl < kK3StatLevels) {
-        kst[lvl] += (unsigned long long)(f.hi - f.lo);
-        kst[kK3StatLevels + lvl] += (unsigned long long)(nL + nR);
-        kst[2 * kK3StatLevels + lvl] += 1ull;
-      } else {
-        add_stats(w, lvl, f.hi - f.lo, nL + nR);
-      }
-    }
-    // children: left [lo, lo+nL) on a->r, right [hi-nR, hi) on r->b
-    Frame cl, cr;
-    cl.ax = f.ax; cl.ay = f.ay; cl.bx = G->rx; cl.by = G->ry;
-    cl.la = l1;
-    cl.lo = f.lo; cl.hi = f.lo + nL; cl.a = f.a; cl.b = r; cl.r = -1; cl.buf = f.buf ^ 1; cl.depth = f.depth + 1;
-    cl.pad = 0;
-    cr.ax = G->rx; cr.ay = G->ry; cr.bx = f.bx; cr.by = f.by;
-    cr.la = l2;
-    cr.lo = f.hi - nR; cr.hi = f.hi; cr.a = r; cr.b = f.b; cr.r = -1; cr.buf = f.buf ^ 1; cr.depth = f.depth + 1;
-    cr.pad = 0;
-    if (lane == 0) {
-      if (nL == 1) { const int u = Pout[cl.lo]; emit(w, (long long)S.off + cl.lo + 1 + S.shift, I[u] - S.set_off); }
-      if (nR == 1) { const int u = Pout[cr.lo]; emit(w, (long long)S.off + cr.lo + 1 + S.shift, I[u] - S.set_off); }
-    }
-    const bool pl = nL >= 2, pr = nR >= 2;
-    const int need = (pl ? 1 : 0) + (pr ? 1 : 0);
-    if (top + need > kK3Stack) {
-      if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
-      return;
-    }
-    if (lane == 0) {
-      // larger child first so the smaller one is processed next (stack depth <= log2 n + 1)
-      if (pl && pr) {
-        if (nL >= nR) { stk[top] = cl; stk[top + 1] = cr; }
-        else { stk[top] = cr; stk[top + 1] = cl; }
-      } else if (pl) {
-        stk[top] = cl;
-      } else if (pr) {
-        stk[top] = cr;
-      }
-    }
-    top += need;
-    __syncwarp();
-#ifdef VQ_K1_PROFILE
-    K3_MARK(q4);
-    kp[6] += q4 - q0;
-#endif
-  }
-#ifdef VQ_K1_PROFILE
-  kp[4] = __reduce_add_sync(kFull, (unsigned)kp[4]);  // per-lane point counts: warp totals
-  kp[5] = __reduce_add_sync(kFull, (unsigned)kp[5]);
-  if (lane == 0)
-    for (int i = 0; i < 7; i++) atomicAdd(&w.ctrl->k3prof[i], kp[i]);
-#endif
-#undef K3_MARK
-}
-
-// Per-level counters of the small-segment kernel are summed per warp in
-// shared memory (levels below kK3StatLevels) and added to the call's
-// counters once, when the warp finishes: one atomic per level and counter
-// instead of one per frame (hull-dense inputs have a frame per vertex).
-static constexpr size_t kK3PerWarp = (size_t)kK3Cap * 24 + sizeof(Frame) * kK3Stack + sizeof(SegGeom) +
-                                     4 * sizeof(double) + 3 * kK3StatLevels * sizeof(unsigned long long);
-
-__global__ void __launch_bounds__(kK3Warps * kWarp) k_k3(Work w) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  if (fatal(w)) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* base = smem + kK3PerWarp * warp;
-  double* X = reinterpret_cast<double*>(base);
-  double* Y = X + kK3Cap;
-  int* I = reinterpret_cast<int*>(Y + kK3Cap);
-  unsigned short* P0 = reinterpret_cast<unsigned short*>(I + kK3Cap);
-  unsigned short* P1 = P0 + kK3Cap;
-  SegGeom* G = reinterpret_cast<SegGeom*>(P1 + kK3Cap);  // 8-byte aligned: 24 * kK3Cap bytes precede it
-  double* E = reinterpret_cast<double*>(G + 1);
-  Frame* stk = reinterpret_cast<Frame*>(E + 4);
-  unsigned long long* kst = reinterpret_cast<unsigned long long*>(stk + kK3Stack);
-  for (int i = lane; i < 3 * kK3StatLevels; i += kWarp) kst[i] = 0ull;
-  __syncwarp();
-  const int nq = min(*reinterpret_cast<volatile int*>(&w.ctrl->k3_count), w.capQ);
-  for (int e = blockIdx.x * kK3Warps + warp; e < nq; e += gridDim.x * kK3Warps) {
-    const SegRec S = w.k3q[e];
-    if (!VQ_OK_IDX(w, 17, (long long)S.off + S.len, 1, (long long)w.N + 1) || !VQ_OK_IDX(w, 18, S.r, 0, w.N))
-      continue;
-    if (S.len > kK3Cap) {
-      if (lane == 0) atomicOr(&w.ctrl->err, kErrInternal);
-      continue;
-    }
-    const double* sx;
-    const double* sy;
-    const int* si = nullptr;
-    if (S.flags & kSegSrcInput) {
-      sx = w.x; sy = w.y;
-    } else {
-      const int b = (S.flags & kSegSrcBuf1) ? 1 : 0;
-      sx = w.bx[b]; sy = w.by[b]; si = w.bi[b];
-    }
-#pragma unroll 4
-    for (int l = lane; l < S.len; l += kWarp) {
-      X[l] = sx[S.off + l];
-      Y[l] = sy[S.off + l];
-      I[l] = si ? si[S.off + l] : S.off + l;
-      P0[l] = (unsigned short)l;
-    }
-    __syncwarp();
-    small_solve(w, S, X, Y, I, P0, P1, stk, G, E, kst, lane);
-    __syncwarp();
-  }
-  // this warp's per-level counters into the call's
-  for (int l = lane; l < kK3StatLevels; l += kWarp) {
-    if (kst[2 * kK3StatLevels + l] == 0ull) continue;
-    atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[l]), kst[l]);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[kMaxLevels + l]), kst[kK3StatLevels + l]);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[2 * kMaxLevels + l]), kst[2 * kK3StatLevels + l]);
-  }
-}
+#include "vq_small.cuh"
 
 // ---------------------------------------------------------------------------
 // K4: order the emitted vertices by key (bitmap compaction)
@@ -1665,23 +1420,24 @@ cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st) {
 // evaluation of orient(a, b, u) that the partition, finalize and pre-filter
 // kernels use: make_line on the exact endpoints, trunc_f32 of the point,
 // orient_f32 with its bound.
-__global__ void k_debug_orient_f32(const double* tri, long long m, float* d, float* e) {
+__global__ void k_debug_orient_f32(const double* tri, long long m, int tier, float* d, float* e) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x) {
     const double* t = tri + 6 * k;
     const LineF L = make_line(t[0], t[1], t[2], t[3]);
     float key, err;
-    line_key_k(L, nullptr, t[4], t[5], key, err);
+    if (tier == 0) line_key_k(L, nullptr, t[4], t[5], key, err);
+    else orient_rel(L, t[0], t[1], t[4], t[5], key, err);
     d[k] = key;
     e[k] = err;
   }
 }
 
-cudaError_t launch_debug_orient_f32(const double* tri, long long m, float* d, float* e, cudaStream_t st) {
+cudaError_t launch_debug_orient_f32(const double* tri, long long m, int tier, float* d, float* e, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   long long blocks = (m + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   count_launch();
-  k_debug_orient_f32<<<(unsigned)blocks, 256, 0, st>>>(tri, m, d, e);
+  k_debug_orient_f32<<<(unsigned)blocks, 256, 0, st>>>(tri, m, tier, d, e);
   return cudaGetLastError();
 }
 
@@ -1727,7 +1483,7 @@ cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int k3_smem_bytes() { return (int)(kK3PerWarp * kK3Warps); }
+int k3_smem_bytes() { return (int)sizeof(K3Smem); }
 
 cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st) {
   static bool attr[64] = {};
@@ -1740,7 +1496,7 @@ cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st) {
     attr[dev] = true;
   }
   count_launch();
-  k_k3<<<grid, kK3Warps * kWarp, k3_smem_bytes(), st>>>(w);
+  k_k3<<<grid, kK3Threads, k3_smem_bytes(), st>>>(w);
   return cudaGetLastError();
 }
 

@@ -350,17 +350,21 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
       account(k, c, key, err);
     }
   }
-  // exact tiers for the undecided points (rare)
+  // the undecided points (rare, but most of them on hull-dense inputs): the
+  // relative FP32 tier, then the exact tiers
   if (__any_sync(kFull, und != 0)) {
     for (unsigned u = und; u != 0; u &= u - 1) {
       const int k = __ffs(u) - 1;
       const int l = k * kWarp + lane;
       const double ux = X[l], uy = Y[l];
-      const int c = classify_exact(G, ux, uy);
+      K key, err;
+      int c = classify_rel(*G, l1, l2, ux, uy, key, err);
+      if (c == 3) {
+        c = classify_exact(G, ux, uy);
+        if (c == 1) line_key_tight(l1, &G->ax, ux, uy, key, err);
+        if (c == 2) line_key_tight(l2, &G->rx, ux, uy, key, err);
+      }
       if (c != 0) {
-        K key, err;
-        if (c == 1) line_key_k(l1, &G->ax, ux, uy, key, err);
-        else line_key_k(l2, &G->rx, ux, uy, key, err);
         const K lo = key_lo(key, err), hi = key_hi(key, err);
         if (c == 1) { m1 |= 1u << k; lo0 = key_max(lo0, lo); hi0 = key_max(hi0, hi); }
         else { m2 |= 1u << k; lo1 = key_max(lo1, lo); hi1 = key_max(hi1, hi); }
@@ -397,13 +401,14 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
     const K thr = have && rlo > Lc ? rlo : Lc;
     const unsigned mc = ch ? m2 : m1;
     const double* E = ch ? &G->rx : &G->ax;
-    // the survivors' keys again (the same evaluation as in pass A, so the
-    // same values): candidates reach the threshold
+    // the survivors' keys again, as tight as the FP32 tiers give them (any
+    // valid bounds will do: the true farthest point's upper bound reaches
+    // every lower bound): candidates reach the threshold
     unsigned cm = 0;
     for (unsigned u = mc; u != 0; u &= u - 1) {
       const int l = (__ffs(u) - 1) * kWarp + lane;
       K key, err;
-      line_key_k(ch ? l2 : l1, E, X[l], Y[l], key, err);
+      line_key_tight(ch ? l2 : l1, E, X[l], Y[l], key, err);
       if (key_hi(key, err) >= thr) cm |= 1u << (__ffs(u) - 1);
     }
     const unsigned lanes = __ballot_sync(kFull, cm != 0);
@@ -414,7 +419,7 @@ __device__ __forceinline__ void k1w_tile(const Work& w, int par, K1Stage<32 * PP
       const int l = (__ffs(u) - 1) * kWarp + lane;
       const double ux = X[l], uy = Y[l];
       K key, err;
-      line_key_k(ch ? l2 : l1, E, ux, uy, key, err);
+      line_key_tight(ch ? l2 : l1, E, ux, uy, key, err);
       take_best(b, E, ux, uy, SRC_INPUT ? begin + l : I[l], key, err);
     }
     if (__popc(lanes) > 1) {

@@ -130,7 +130,7 @@ def load(build_if_missing: bool = True):
         lib.vq_profile_read.restype = ctypes.c_int
         lib.vq_autotune.argtypes = [vp, vp, i64, i32, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_double), vp]
         lib.vq_autotune.restype = ctypes.c_int
-        lib.vq_debug_orient_f32.argtypes = [vp, i64, vp, vp, vp]
+        lib.vq_debug_orient_f32.argtypes = [vp, i64, i32, vp, vp, vp]
         lib.vq_debug_orient_f32.restype = ctypes.c_int
         lib.vq_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
         lib.vq_server_create.restype = ctypes.c_int
@@ -274,9 +274,10 @@ def vq_set_config(cfg: Config | None = None, **kw) -> Config:
     return c
 
 
-def vq_debug_orient_f32(tri: torch.Tensor, stream=None):
-    """The FP32 tier's value and bound of orient(a, b, u) for device FP64
-    triples tri[k] = (ax, ay, bx, by, ux, uy): returns (d, e) on the device."""
+def vq_debug_orient_f32(tri: torch.Tensor, tier: int = 0, stream=None):
+    """An FP32 tier's value and bound of orient(a, b, u) for device FP64
+    triples tri[k] = (ax, ay, bx, by, ux, uy) (tier 0: absolute
+    coordinates, 1: relative to a): returns (d, e) on the device."""
     lib = load()
     if not isinstance(tri, torch.Tensor) or tri.device.type != "cuda" or tri.dtype != torch.float64:
         raise TypeError("tri must be a CUDA float64 tensor")
@@ -284,7 +285,7 @@ def vq_debug_orient_f32(tri: torch.Tensor, stream=None):
     m = t.shape[0]
     d = torch.empty(m, dtype=torch.float32, device=t.device)
     e = torch.empty(m, dtype=torch.float32, device=t.device)
-    _check(lib.vq_debug_orient_f32(t.data_ptr(), m, d.data_ptr(), e.data_ptr(), _stream_ptr(stream)),
+    _check(lib.vq_debug_orient_f32(t.data_ptr(), m, int(tier), d.data_ptr(), e.data_ptr(), _stream_ptr(stream)),
            "vq_debug_orient_f32")
     return d, e
 

@@ -7,7 +7,11 @@ line's truncated origin and rounded direction and on the point truncated to
 |d| > E, so every hull claimed exact rests on |d - orient| <= E.  This test
 runs the device's own evaluation (vq_debug_orient_f32, the code the kernels
 inline) on more than a million near-degenerate triples and checks the bound
-against the exact orient, computed by the oracle's big-integer sums.
+against the exact orient, computed by the oracle's big-integer sums.  The
+same holds for the second FP32 tier, which evaluates the test in coordinates
+relative to the line's origin for the points the first leaves undecided
+(nearly collinear, far from the origin: points on a circle), and which must
+decide most of the circle-arc triples that the first cannot.
 """
 import numpy as np
 import pytest
@@ -53,27 +57,54 @@ def near_degenerate_triples(rng, m):
     w = rng.random(m) * 1.5 - 0.25
     u = a + w[:, None] * (b - a)
     u[lat] = a[lat] + rng.integers(-4, 5, (lat.sum(), 1)) * (b[lat] - a[lat])
-    # a few ulps off the line (not for the generic kind)
-    near = kind != 5
+    # a few ulps off the line (not for the generic kind nor the arcs)
+    near = (kind != 5) & (kind != 4)
     u[near] += rng.integers(-4, 5, (near.sum(), 2)) * np.spacing(np.abs(u[near]))
     gen = kind == 5
     u[gen] = (rng.random((gen.sum(), 2)) * 2 - 1) * s[gen]
+    # points on a circle arc between a and b (hull-dense data: nearly
+    # collinear with the chord, far from the origin relative to its length)
+    arc = kind == 4
+    na = int(arc.sum())
+    th = rng.random(na) * 2 * np.pi
+    dth = np.ldexp(1.0, rng.integers(-30, -4, na))
+    rad = np.ldexp(1.0, rng.integers(-20, 39, na))[:, None]
+    ang = np.stack([th, th + dth, th + dth * rng.random(na)], 1)
+    pts = np.stack([np.cos(ang), np.sin(ang)], 2) * rad[:, :, None]
+    a[arc], b[arc], u[arc] = pts[:, 0], pts[:, 1], pts[:, 2]
     tri = np.concatenate([a, b, u], axis=1)
     tri = np.where(np.abs(tri) < 2.0 ** 40, tri, np.copysign(2.0 ** 39, tri))
     return tri
 
 
-def test_fp32_tier_bound_holds(vq):
+def test_fp32_tiers_bound_holds(vq):
+    """Both FP32 tiers on the same 1.2M triples (tier 0: absolute
+    coordinates; tier 1: relative to the line's origin): the bound holds for
+    each, and the relative tier decides far more of the circle arcs."""
     rng = np.random.default_rng(2510)
-    tri = near_degenerate_triples(rng, 1_200_000)
+    m = 1_200_000
+    tri = near_degenerate_triples(rng, m)
     assert np.all(np.isfinite(tri)) and np.all(np.abs(tri) < 2.0 ** 40)
-    d, e = vq.vq_debug_orient_f32(torch.from_numpy(tri).cuda())
-    d, e = d.cpu().numpy(), e.cpu().numpy()
-    assert np.all(np.isfinite(d)) and np.all(e >= 0)
-    out, bad = oracle.orient_bound_check(tri, d, e)
-    assert out == 0, f"{out} triples with |d - orient| > E"
-    assert bad == 0, f"{bad} signs claimed wrong"
-    # the test reaches both sides of the margin: many decided (mostly the
-    # generic sixth of the triples), most of the near-degenerate ones not
-    decided = np.abs(d) > e
-    assert 0.1 < decided.mean() < 0.9, decided.mean()
+    arcs = _arc_rows(2510, m)
+    got = {}
+    for tier in (0, 1):
+        d, e = vq.vq_debug_orient_f32(torch.from_numpy(tri).cuda(), tier=tier)
+        d, e = d.cpu().numpy(), e.cpu().numpy()
+        assert np.all(np.isfinite(d)) and np.all(e >= 0)
+        out, bad = oracle.orient_bound_check(tri, d, e)
+        assert out == 0, f"tier {tier}: {out} triples with |d - orient| > E"
+        assert bad == 0, f"tier {tier}: {bad} signs claimed wrong"
+        got[tier] = np.abs(d) > e
+    # both sides of the margin are reached: many decided, many not
+    assert 0.1 < got[0].mean() < 0.9, got[0].mean()
+    # the arcs: the absolute tier decides few, the relative one many
+    assert got[1][arcs].mean() > 0.3 and got[1][arcs].mean() > 3 * got[0][arcs].mean(), \
+        (got[0][arcs].mean(), got[1][arcs].mean())
+
+
+def _arc_rows(rng_seed, m):
+    """The rows of near_degenerate_triples(default_rng(rng_seed), m) that
+    are circle arcs (the generator draws the kinds first)."""
+    rng = np.random.default_rng(rng_seed)
+    rng.integers(-60, 40, m)
+    return rng.integers(0, 6, m) == 4
