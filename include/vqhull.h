@@ -79,6 +79,18 @@ vq_status vq_hull2d(const double* x, const double* y, int64_t n, int32_t* hull_i
                     void* stream);
 
 /*
+ * vq_hull2d on interleaved points: xy holds x0, y0, x1, y1, ... (device FP64,
+ * 2n values, 8-byte aligned; 16-byte alignment gives the fastest loads), the
+ * array-of-structures layout of PBBS's point files that the paper's
+ * comparison with PBBS describes (Sec. 5.4).  The hull and its indices are
+ * those of vq_hull2d on the same points.  The interleaved array is read once
+ * by the level-0 pre-filter pass (which this call always uses); the points
+ * it keeps continue in the library's own SoA buffers.  Arguments, errors and
+ * stream behaviour as for vq_hull2d.
+ */
+vq_status vq_hull2d_aos(const double* xy, int64_t n, int32_t* hull_idx, int64_t* h, void* stream);
+
+/*
  * Hulls of nsets independent point sets in one level-synchronous run: the
  * result per set is that of Alg. 1 (Sec. 2.1), and every level of the
  * subset extraction (Sec. 3: classify, compact, farthest point) runs over

@@ -370,9 +370,13 @@ static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cach
 // shared-memory recursion, which walks one hull vertex per step).
 static vq_status run(Ctx& c, const double* x, const double* y, const long long* offsets, long long n_single,
                      int nsets, long long N, int* out, long long* hull_offsets, long long* h_out,
-                     cudaStream_t st, int small_max_override = 0) {
+                     cudaStream_t st, int small_max_override = 0, int aos = 0) {
   Config cfg = get_cfg();
   if (small_max_override > 0) cfg.small_max = small_max_override;
+  if (aos) {  // interleaved points are read by the sieve only (the pre-filter path)
+    cfg.prefilter = 1;
+    cfg.ordered = 0;
+  }
   const long long nkeys = N + nsets;
   Work w;
   memset(&w, 0, sizeof w);
@@ -384,6 +388,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   long long* scan_tmp = reinterpret_cast<long long*>(c.mem + main_bytes);
   w.x = x;
   w.y = y;
+  w.aos = aos;
   w.offsets = offsets;
   w.key_base = nullptr;
   w.n_single = n_single;
@@ -631,6 +636,23 @@ vq_status vq_hull2d(const double* x, const double* y, int64_t n, int32_t* hull_i
   if ((s = ctx_init(*c)) != VQ_OK) return s;
   long long hh = 0;
   s = run(*c, x, y, nullptr, n, 1, n, hull_idx, nullptr, &hh, static_cast<cudaStream_t>(stream));
+  *h = hh;
+  return s;
+}
+
+vq_status vq_hull2d_aos(const double* xy, int64_t n, int32_t* hull_idx, int64_t* h, void* stream) {
+  if (!h || n < 0) return VQ_ERR_INVALID_ARG;
+  *h = 0;
+  if (n == 0) return VQ_OK;
+  if (!xy || !hull_idx || (reinterpret_cast<uintptr_t>(xy) & 7u) != 0) return VQ_ERR_INVALID_ARG;
+  if (n > (int64_t)INT_MAX - 2) return VQ_ERR_TOO_LARGE;
+  vq_status s;
+  Ctx* c = current_ctx(s);
+  if (!c) return s;
+  std::lock_guard<std::mutex> g(c->mu);
+  if ((s = ctx_init(*c)) != VQ_OK) return s;
+  long long hh = 0;
+  s = run(*c, xy, xy + 1, nullptr, n, 1, n, hull_idx, nullptr, &hh, static_cast<cudaStream_t>(stream), 0, 1);
   *h = hh;
   return s;
 }

@@ -22,6 +22,10 @@ __device__ __forceinline__ bool vq_check_idx(const Work& w, int site, long long 
 #define VQ_OK_IDX(w, site, v, lo, hi) true
 #endif
 
+// Coordinates of the caller's point i (structure of arrays, or interleaved).
+__device__ __forceinline__ double px(const Work& w, long long i) { return w.x[w.aos ? 2 * i : i]; }
+__device__ __forceinline__ double py(const Work& w, long long i) { return w.y[w.aos ? 2 * i : i]; }
+
 __device__ __forceinline__ bool fatal(const Work& w) {
   return (*reinterpret_cast<volatile unsigned*>(&w.ctrl->err) & kErrFatal) != 0;
 }

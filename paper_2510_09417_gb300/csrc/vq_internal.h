@@ -25,8 +25,9 @@ constexpr int kFillTiles = 1024;    // tiles per tile-map fill job
 
 // Everything a kernel needs, passed by value.
 struct Work {
-  const double* x;           // caller's points (global index = position)
-  const double* y;
+  const double* x;           // caller's points (global index = position): x[i], y[i], or with
+  const double* y;           // aos set, x = xy, y = xy + 1 and point i at xy[2 i], xy[2 i + 1]
+  int aos;                   // 1: the caller's points are interleaved (x0, y0, x1, y1, ...)
   const long long* offsets;  // nsets + 1 device offsets, or null (single set of n_single)
   const long long* key_base; // optional per-set key of p (server); null: off + set
   long long n_single;

@@ -89,7 +89,7 @@ __device__ int push_k1_warp(const Work& w, int par, SegRec R, int lane) {
   if (lane == 0) {
     w.segs[par][slot] = R;
     SegGeom g;
-    fill_geom(g, w.x[R.a], w.y[R.a], w.x[R.b], w.y[R.b], w.x[R.r], w.y[R.r]);
+    fill_geom(g, px(w, R.a), py(w, R.a), px(w, R.b), py(w, R.b), px(w, R.r), py(w, R.r));
     w.geom[par][slot] = g;
   }
   for (int i = lane; i < njobs; i += kWarp)

@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(256) k_sample(Work w) {
 #pragma unroll
     for (int q = 0; q < kSamplePPT; q++) {
       const int l = q * 256 + (int)threadIdx.x;
-      vx[q] = l < count ? w.x[begin + l] : 0.0;
-      vy[q] = l < count ? w.y[begin + l] : 0.0;
+      vx[q] = l < count ? px(w, begin + l) : 0.0;
+      vy[q] = l < count ? py(w, begin + l) : 0.0;
     }
     float fx[kSamplePPT], fy[kSamplePPT];
 #pragma unroll
@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(128) k_poly(Work w) {
     double x = 0.0, y = 0.0;
     bool ok = true;
     if (idx >= 0) {
-      x = w.x[idx];
-      y = w.y[idx];
+      x = px(w, idx);
+      y = py(w, idx);
       const unsigned ax = static_cast<unsigned>(__double2hiint(x)) & 0x7fffffffu;
       const unsigned ay = static_cast<unsigned>(__double2hiint(y)) & 0x7fffffffu;
       ok = max(ax, ay) < 0x42700000u;  // |coordinate| < 2^40, finite
@@ -426,32 +426,41 @@ __global__ void __launch_bounds__(32 * kSvWarps, 3) k_sieve(Work w) {
   for (int t = t0; t < t1; t++) {
     const int j = t - w.k0_tile_start[set];
     const int tb = S.off + j * kK0Tile, tc = min(kK0Tile, S.len - j * kK0Tile);
-    const bool vec = ((reinterpret_cast<uintptr_t>(w.x + tb) | reinterpret_cast<uintptr_t>(w.y + tb)) & 15u) == 0;
+    const bool vec = w.aos ? (reinterpret_cast<uintptr_t>(w.x + 2ll * tb) & 15u) == 0
+                           : ((reinterpret_cast<uintptr_t>(w.x + tb) | reinterpret_cast<uintptr_t>(w.y + tb)) & 15u) == 0;
     for (int s0 = warp * kSvStep; s0 < tc; s0 += kSvWarps * kSvStep) {
       const int base = tb + s0, cnt = min(kSvStep, tc - s0);
-      double px[8], py[8];
-      if (vec && cnt == kSvStep) {
+      double vx[8], vy[8];
+      if (vec && cnt == kSvStep && !w.aos) {
         const double2* X2 = reinterpret_cast<const double2*>(w.x + base);
         const double2* Y2 = reinterpret_cast<const double2*>(w.y + base);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
           const double2 a = __ldcs(X2 + k * kWarp + lane), b = __ldcs(Y2 + k * kWarp + lane);
-          px[2 * k] = a.x; px[2 * k + 1] = a.y;
-          py[2 * k] = b.x; py[2 * k + 1] = b.y;
+          vx[2 * k] = a.x; vx[2 * k + 1] = a.y;
+          vy[2 * k] = b.x; vy[2 * k + 1] = b.y;
+        }
+      } else if (vec && cnt == kSvStep) {  // interleaved: one 16-byte load per point
+        const double2* P2 = reinterpret_cast<const double2*>(w.x + 2ll * base);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const double2 a = __ldcs(P2 + 64 * (q >> 1) + 2 * lane + (q & 1));
+          vx[q] = a.x;
+          vy[q] = a.y;
         }
       } else {
 #pragma unroll
         for (int q = 0; q < 8; q++) {
           const int l = 64 * (q >> 1) + 2 * lane + (q & 1);
-          px[q] = l < cnt ? w.x[base + l] : 0.0;
-          py[q] = l < cnt ? w.y[base + l] : 0.0;
+          vx[q] = l < cnt ? px(w, base + l) : 0.0;
+          vy[q] = l < cnt ? py(w, base + l) : 0.0;
         }
       }
       unsigned rest = 0;
 #pragma unroll
       for (int q = 0; q < 8; q++) {
         const int l = 64 * (q >> 1) + 2 * lane + (q & 1);
-        if (l < cnt && !in_boxes(bx, hword(px[q]), hword(py[q]))) rest |= 1u << q;
+        if (l < cnt && !in_boxes(bx, hword(vx[q]), hword(vy[q]))) rest |= 1u << q;
       }
       if (!__any_sync(kFull, rest != 0)) continue;
       // the points outside the boxes, compacted into the warp's list
@@ -462,8 +471,8 @@ __global__ void __launch_bounds__(32 * kSvWarps, 3) k_sieve(Work w) {
         const unsigned b = __ballot_sync(kFull, o);
         if (o) {
           const int d = n + __popc(b & lt);
-          R.x[d] = px[q];
-          R.y[d] = py[q];
+          R.x[d] = vx[q];
+          R.y[d] = vy[q];
           R.i[d] = base + 64 * (q >> 1) + 2 * lane + (q & 1);
         }
         n += __popc(b);

@@ -89,7 +89,7 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
     M.fr[0] = (short)r0;
   }
   for (int k = 0; k < kK3PPT; k++) {
-    const int q = tid + k * kK3Threads;
+    const int q = tid * kK3PPT + k;
     M.P[0][q] = (unsigned short)q;
     M.FR[0][q] = q < len ? 0 : kNoFrame;
   }
@@ -103,7 +103,7 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
       double klo[kK3PPT], khi[kK3PPT];
 #pragma unroll
       for (int k = 0; k < kK3PPT; k++) {
-        const int q = tid + k * kK3Threads;
+        const int q = tid * kK3PPT + k;
         klo[k] = -INFINITY;
         khi[k] = -INFINITY;
         const int f = M.FR[cur][q];
@@ -121,20 +121,16 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
       int c = 0;
 #pragma unroll
       for (int k = 0; k < kK3PPT; k++) {
-        const int q = tid + k * kK3Threads;
+        const int q = tid * kK3PPT + k;
         const int f = M.FR[cur][q];
         if (f != kNoFrame && khi[k] >= dkey_inv(M.kmax[f])) { cm |= 1u << k; c++; }
       }
-      // position order is k-major across threads: scan per k
+      // a thread holds consecutive positions: one scan gives position order
       int total = 0;
+      int pos = k3_scan(c, M.wsum, &total);
 #pragma unroll
-      for (int k = 0; k < kK3PPT; k++) {
-        int t;
-        const int b = (cm >> k) & 1u;
-        const int pos = k3_scan(b, M.wsum, &t);
-        if (b) M.cand[total + pos] = (unsigned short)(tid + k * kK3Threads);
-        total += t;
-      }
+      for (int k = 0; k < kK3PPT; k++)
+        if ((cm >> k) & 1u) M.cand[pos++] = (unsigned short)(tid * kK3PPT + k);
       if (tid == 0) M.ncand = total;
       __syncthreads();
       // each frame's candidates are adjacent in the list: its range
@@ -182,13 +178,13 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
       M.nl[f] = 0;
       M.nr[f] = 0;
     }
-    for (int k = 0; k < kK3PPT; k++) M.FR[nxt][tid + k * kK3Threads] = kNoFrame;
+    for (int k = 0; k < kK3PPT; k++) M.FR[nxt][tid * kK3PPT + k] = kNoFrame;
     __syncthreads();
     // C. classify every point of every frame; move it to its child's range
     int npos[kK3PPT], ncls[kK3PPT], nfr[kK3PPT];
 #pragma unroll
     for (int k = 0; k < kK3PPT; k++) {
-      const int q = tid + k * kK3Threads;
+      const int q = tid * kK3PPT + k;
       ncls[k] = 0;
       npos[k] = 0;
       nfr[k] = 0;
@@ -303,8 +299,8 @@ __global__ void __launch_bounds__(kK3Threads) k_k3(Work w) {
     }
     __syncthreads();  // the previous segment is done with M
     if (threadIdx.x == 0) {
-      M.X[kK3Cap] = w.x[S.a]; M.Y[kK3Cap] = w.y[S.a]; M.I[kK3Cap] = S.a;
-      M.X[kK3Cap + 1] = w.x[S.b]; M.Y[kK3Cap + 1] = w.y[S.b]; M.I[kK3Cap + 1] = S.b;
+      M.X[kK3Cap] = px(w, S.a); M.Y[kK3Cap] = py(w, S.a); M.I[kK3Cap] = S.a;
+      M.X[kK3Cap + 1] = px(w, S.b); M.Y[kK3Cap + 1] = py(w, S.b); M.I[kK3Cap + 1] = S.b;
       M.ncand = INT_MAX;
     }
     __syncthreads();

@@ -84,7 +84,7 @@ class ServerInfo(ctypes.Structure):
 
 
 SYMBOLS = (
-    "vq_status_string", "vq_version", "vq_hull2d", "vq_hull2d_batched", "vq_hull2d_host", "vq_hull2d_noalloc",
+    "vq_status_string", "vq_version", "vq_hull2d", "vq_hull2d_aos", "vq_hull2d_batched", "vq_hull2d_host", "vq_hull2d_noalloc",
     "vq_get_config", "vq_set_config", "vq_last_stats", "vq_profile_read", "vq_autotune", "vq_debug_orient_f32",
     "vq_server_create", "vq_server_submit",
     "vq_server_poll", "vq_server_wait", "vq_server_wait_any", "vq_server_stats", "vq_server_info_read", "vq_server_destroy",
@@ -114,6 +114,8 @@ def load(build_if_missing: bool = True):
         lib.vq_version.restype = ctypes.c_int
         lib.vq_hull2d.argtypes = [vp, vp, i64, vp, i64p, vp]
         lib.vq_hull2d.restype = ctypes.c_int
+        lib.vq_hull2d_aos.argtypes = [vp, i64, vp, i64p, vp]
+        lib.vq_hull2d_aos.restype = ctypes.c_int
         lib.vq_hull2d_batched.argtypes = [vp, vp, vp, i32, vp, vp, vp]
         lib.vq_hull2d_batched.restype = ctypes.c_int
         lib.vq_hull2d_host.argtypes = [vp, vp, i64, vp, i64p, vp]
@@ -199,6 +201,26 @@ def vq_hull2d(x: torch.Tensor, y: torch.Tensor, hull_idx: torch.Tensor | None = 
     h = ctypes.c_int64(0)
     st = lib.vq_hull2d(x.data_ptr(), y.data_ptr(), n, hull_idx.data_ptr(), ctypes.byref(h), _stream_ptr(stream))
     _check(st, "vq_hull2d")
+    return hull_idx[: h.value]
+
+
+def vq_hull2d_aos(xy: torch.Tensor, hull_idx: torch.Tensor | None = None, stream=None):
+    """Hull of one point set given interleaved: xy is an (n, 2) (or 2n-long)
+    float64 CUDA tensor of (x, y) pairs.  Returns hull_idx[:h] as vq_hull2d."""
+    lib = load()
+    if not isinstance(xy, torch.Tensor) or not xy.is_cuda or xy.dtype != torch.float64:
+        raise TypeError("xy must be a float64 CUDA tensor")
+    xy = xy.contiguous().reshape(-1)
+    if xy.numel() % 2:
+        raise ValueError("xy holds an odd number of values")
+    n = xy.numel() // 2
+    if hull_idx is None:
+        hull_idx = torch.empty(max(n, 1), dtype=torch.int32, device=xy.device)
+    elif hull_idx.dtype != torch.int32 or hull_idx.numel() < n or not hull_idx.is_cuda:
+        raise ValueError("hull_idx must be an int32 CUDA tensor with room for n indices")
+    h = ctypes.c_int64(0)
+    _check(lib.vq_hull2d_aos(xy.data_ptr(), n, hull_idx.data_ptr(), ctypes.byref(h), _stream_ptr(stream)),
+           "vq_hull2d_aos")
     return hull_idx[: h.value]
 
 

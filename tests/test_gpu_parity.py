@@ -356,3 +356,20 @@ def test_prefilter_degenerate_candidates(vq):
     cases.append((g[0], g[1]))
     for x, y in cases:
         check(vq, x, y)
+
+
+@pytest.mark.parametrize("dist", synth.DISTRIBUTIONS)
+def test_aos_entry_point(vq, dist):
+    """Interleaved (x, y) pairs (PBBS's layout, Sec. 5.4): the same hull as
+    the oracle's on the de-interleaved points, also from an odd starting
+    offset (8-byte but not 16-byte aligned) and in a batch of sizes that
+    leave ragged last tiles."""
+    for n, seed in ((3, 1), (1000, 2), (70_001, 3), (1_000_003, 4)):
+        x, y = synth.points(dist, n, 40 + seed)
+        want = oracle.hull(x, y)
+        xy = torch.from_numpy(np.stack([x, y], 1)).cuda()
+        assert np.array_equal(vq.vq_hull2d_aos(xy).cpu().numpy(), want), (dist, n)
+        # one value before the pairs: the array starts 8 bytes past a 16-byte boundary
+        buf = torch.empty(2 * n + 1, dtype=torch.float64, device="cuda")
+        buf[1:] = xy.reshape(-1)
+        assert np.array_equal(vq.vq_hull2d_aos(buf[1:]).cpu().numpy(), want), (dist, n, "offset")
