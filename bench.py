@@ -119,7 +119,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration hull times")
-    ap.add_argument("--serving-requests", type=int, default=128)
+    ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--profile-one", default="", choices=[""] + list(synth.DISTRIBUTIONS),
                     help="profiling aid: run --profile-reps hulls of --n points of this distribution "
                          "(the workload's seed), print their counters and exit")
@@ -322,8 +322,9 @@ def bench_serving(vq, torch, nreq, budget=40 << 30, lanes=3):
                       "served": {"p50_ms": pct(ls, 50), "p99_ms": pct(ls, 99), "hulls_per_s": nreq / ws_,
                                  "admitted_while_busy": inf["admitted_while_busy"],
                                  "max_busy_lanes": inf["max_busy_lanes"], "batches": inf["batches"]}})
-    return {"workload": f"{nreq} requests, sizes log-uniform in [100, 1e7] FP64 points, distributions mixed, "
-                        "Poisson arrivals (seed 6); host points (pageable) copied in per request",
+    return {"workload": f"{nreq} requests per rate, sizes log-uniform in [100, 1e7] FP64 points, distributions "
+                        "mixed, Poisson arrivals (seed 6); the plain path copies each request from pageable host "
+                        "memory, the server stages submitted points in its pinned area",
             "points": int(sum(r["n"] for r in reqs)), "budget_bytes": budget, "lanes": lanes,
             "saturated": {"plain_hulls_per_s": sat_plain, "served_hulls_per_s": sat_served,
                           "plain_p50_ms": pct(lat_p, 50), "plain_p99_ms": pct(lat_p, 99),

@@ -266,6 +266,10 @@ typedef struct {
   int32_t device;          /* CUDA device ordinal                            */
   int32_t lanes;           /* batches on the device at once, each on its own
                               stream (1..16; 0 = default 3)                   */
+  size_t pinned_bytes;     /* pinned host memory that stages submitted points
+                              (0: the smaller of the budget and 8 GiB); a
+                              request that does not fit is kept in pageable
+                              memory instead                                  */
 } vq_server_config;
 
 /*
@@ -286,8 +290,8 @@ typedef struct {
  */
 vq_status vq_server_create(const vq_server_config* cfg, vq_server** out);
 
-/* Queues a hull of n host points (copied before return; the caller may free
- * them).  VQ_ERR_BUDGET if the request alone (its batch's device bytes plus
+/* Queues a hull of n host points (copied before return, into the server's
+ * pinned staging area when it has room; the caller may free them).  VQ_ERR_BUDGET if the request alone (its batch's device bytes plus
  * the server's fixed 1 MiB reserve) exceeds the memory budget.  Serving
  * only; no counterpart in the paper. */
 vq_status vq_server_submit(vq_server* s, const double* x_host, const double* y_host, int64_t n,

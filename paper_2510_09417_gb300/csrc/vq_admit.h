@@ -1,9 +1,12 @@
-// vq_admit.h -- admission policy of the serving handle (host code only, no
-// CUDA): which queued requests an idle lane takes as its next batch.
+// vq_admit.h -- host-side policies of the serving handle (no CUDA): which
+// queued requests an idle lane takes as its next batch, and the first-fit
+// extents of the pinned area that stages submitted points.
 #pragma once
 
 #include <cstddef>
 #include <cstdint>
+#include <iterator>
+#include <map>
 
 namespace vq {
 
@@ -31,5 +34,48 @@ inline int admit_prefix(const int64_t* sizes, int nqueued, long long resident, s
   *batch_bytes = b;
   return k;
 }
+
+// Free extents of a staging area (offset -> bytes): first-fit takes, and
+// returns merged with their free neighbours.
+class Extents {
+ public:
+  // an extent of `bytes` at *off; false when no free extent is that large
+  bool take(size_t bytes, size_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes, at = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[at] = rest;
+      return true;
+    }
+    return false;
+  }
+  void give(size_t off, size_t bytes) {
+    if (!bytes) return;
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + bytes == next->first) {
+      bytes += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += bytes;
+        return;
+      }
+    }
+    free_[off] = bytes;
+  }
+  size_t extents() const { return free_.size(); }
+  size_t largest() const {
+    size_t m = 0;
+    for (const auto& kv : free_) m = kv.second > m ? kv.second : m;
+    return m;
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+};
 
 }  // namespace vq

@@ -76,10 +76,6 @@ struct LevelGraph {
   unsigned long long used = 0;
 };
 constexpr int kGraphCache = 16;           // graphs kept per device (least recently used goes)
-// Capturing and instantiating a graph costs about as much as a few host
-// round trips, so smaller runs keep the host loop unless their graph is
-// already cached.
-constexpr long long kGraphMinPoints = 1ll << 22;
 constexpr int kGraphKernelsPerIter = 13;  // two levels of 6 kernels (two partition tiers), and the condition
 
 struct Ctx {
@@ -91,6 +87,8 @@ struct Ctx {
   size_t bytes = 0;
   bool external = false;   // mem belongs to the caller (server lanes): never freed or grown here
   Ctrl* h_ctrl = nullptr;  // pinned
+  Work* d_work = nullptr;  // the call's Work in device memory (the level loop's kernels read it)
+  Work* h_work = nullptr;  // pinned source of its copy
   long long* h_total = nullptr;
   // staging for vq_hull2d_host
   double* stage = nullptr;
@@ -248,6 +246,8 @@ static vq_status ctx_init(Ctx& c) {
   VQ_CHECK(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device));
   VQ_CHECK(cudaMallocHost(&c.h_ctrl, sizeof(Ctrl) + 64));
   c.h_total = reinterpret_cast<long long*>(reinterpret_cast<char*>(c.h_ctrl) + sizeof(Ctrl) + 32);
+  VQ_CHECK(cudaMallocHost(&c.h_work, sizeof(Work)));
+  VQ_CHECK(cudaMalloc(&c.d_work, sizeof(Work)));
   c.init = true;
   return VQ_OK;
 }
@@ -295,10 +295,11 @@ static void graph_free(LevelGraph& g) {
 // `w` is cached yet.
 static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cached_only, cudaGraphExec_t* out) {
   *out = nullptr;
-  std::vector<unsigned char> key(sizeof(Work) + 2 * sizeof(int));
-  memcpy(key.data(), &w, sizeof(Work));
-  memcpy(key.data() + sizeof(Work), &cfg.ppt, sizeof(int));
-  memcpy(key.data() + sizeof(Work) + sizeof(int), &c.sms, sizeof(int));
+  // the kernels read the call's Work from c.d_work: the graph depends only
+  // on what shapes its launches (points per lane, block shape, SM count)
+  const int kv[3] = {cfg.ppt, cfg.k1_shape, c.sms};
+  std::vector<unsigned char> key(sizeof kv);
+  memcpy(key.data(), kv, sizeof kv);
   for (LevelGraph& g : c.graphs)
     if (g.key == key) {
       g.used = ++c.graph_clock;
@@ -329,7 +330,6 @@ static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cach
     e = cudaStreamBeginCaptureToGraph(c.gstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
       const long long before = kernels_launched();
-      const long long max_iters = (long long)w.N / 2 + 4;
       cudaStream_t gs = c.gstream;
       for (int level = 1; level <= 2 && e == cudaSuccess; level++) {
         if (e == cudaSuccess) e = launch_prologue(w, level, gs);
@@ -338,7 +338,7 @@ static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cach
         if (e == cudaSuccess) e = launch_tilemap(w, (level + 1) & 1, c.sms * 4, gs);
         if (e == cudaSuccess) e = launch_k3(w, c.sms * 2, gs);
       }
-      if (e == cudaSuccess) e = launch_level_cond(w, h, max_iters, gs);
+      if (e == cudaSuccess) e = launch_level_cond(w, h, gs);
       cudaGraph_t captured = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(gs, &captured);
       if (e == cudaSuccess) e = e2;
@@ -400,6 +400,13 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   w.k1_shape = cfg.k1_shape;
   c.d_stats = w.stats;
 
+  // the level loop's kernels read Work from device memory (one copy per
+  // call; h_work is not rewritten before the call's final synchronisation)
+  w.dev = c.d_work;
+  w.tier_dev = 0;
+  *c.h_work = w;
+  VQ_CHECK(cudaMemcpyAsync(c.d_work, c.h_work, sizeof(Work), cudaMemcpyHostToDevice, st));
+
   const long long launches0 = kernels_launched();
   Timer tm(c, st, cfg.profile != 0);
   VQ_CHECK(tm.begin(kKindOther));
@@ -442,7 +449,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
     // the partition kernel's tier is picked on the device, so the call has
     // no host round trip before its end
     w.tier_dev = 1;
-    if (level_graph(c, w, cfg, N < kGraphMinPoints, &ex) != VQ_OK) {
+    if (level_graph(c, w, cfg, false, &ex) != VQ_OK) {
       c.graph_off = true;  // nothing was launched: the host loop runs instead
       ex = nullptr;
       fprintf(stderr, "vqhull: the device-driven level loop could not be built; using the host loop\n");
@@ -563,6 +570,8 @@ void ctx_destroy(Ctx* c) {
   if (c->gstream) cudaStreamDestroy(c->gstream);
   if (c->cstream) cudaStreamDestroy(c->cstream);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->h_work) cudaFreeHost(c->h_work);
+  if (c->d_work) cudaFree(c->d_work);
   if (c->mem && !c->external) cudaFree(c->mem);
   if (c->stage) cudaFree(c->stage);
   if (c->stage_out) cudaFree(c->stage_out);

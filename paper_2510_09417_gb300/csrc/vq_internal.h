@@ -61,8 +61,11 @@ struct Work {
   int ordered;               // 1: offsets by decoupled look-back (stable layout); 0: atomic cursors
   int all_fast;              // host's copy of !Ctrl::any_slow: selects the FP32-only partition kernel
   int k1_shape;              // streaming partition kernel: block shape 0..2 (warps per block, ring stages)
-  int tier_dev;              // 1: both partition kernels are launched and the device's Ctrl::any_slow
-                             // picks the one that runs (no host round trip); all_fast is then unused
+  int tier_dev;              // host side: 1: both partition kernels are launched and the device's
+                             // Ctrl::any_slow picks the one that runs (no host round trip)
+  const Work* dev;           // this struct's copy in device memory: the kernels of the level loop
+                             // (prologue, partition, finalize, tile map, finisher, loop tests)
+                             // read it there, so a captured level loop serves every call
   PolyF* poly;               // per set: pre-filter chains and inner box
   unsigned long long* dirbest;  // per set and sampled direction: packed (score, index) of the extreme
   int* nsurv;                // per set: points the sieve kept (written to buffer 1 from the set's offset)
@@ -79,7 +82,7 @@ cudaError_t launch_poly(const Work& w, cudaStream_t st);
 cudaError_t launch_sieve(const Work& w, cudaStream_t st);
 cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st);
 // condition kernel of the device-driven level loop (a graph WHILE node)
-cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, long long max_iters, cudaStream_t st);
+cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, cudaStream_t st);
 // a kernel node of graph g (no dependencies) that sets h to whether the
 // level after level 0 has segments (the WHILE node's first test)
 cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphNode_t* node, const Work& w, cudaGraphConditionalHandle h);

@@ -101,7 +101,8 @@ __device__ int push_k1_warp(const Work& w, int par, SegRec R, int lane) {
 
 // The per-tile map of level parity `par`: segment, look-back status word
 // and the partition kernel's tile descriptor, one fill job per block.
-__global__ void __launch_bounds__(256) k_tilemap(Work w, int par) {
+__global__ void __launch_bounds__(256) k_tilemap(const Work* __restrict__ wp, int par) {
+  const Work& w = *wp;
   if (fatal(w)) return;
   const int njobs = min(*reinterpret_cast<volatile int*>(&w.ctrl->fill_jobs[par]), w.capJ);
   for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
@@ -452,7 +453,8 @@ __device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, c
   }
 }
 
-__global__ void k_prologue(Work w, int level) {
+__global__ void k_prologue(const Work* __restrict__ wp, int level) {
+  const Work& w = *wp;
   const int par = level & 1;
   w.ctrl->k1_ticket = 0;
   w.ctrl->k1_segs[par ^ 1] = 0;
@@ -469,7 +471,8 @@ __global__ void k_prologue(Work w, int level) {
 // body runs two partition levels (parity 1, then parity 0).  The loop goes
 // on while the next level (parity 1) has segments and no fatal error was
 // raised.  Every level removes at least one point from each of its
-// segments, so max_iters bounds the loop; reaching it is an internal error.
+// segments, so N / 2 + 4 iterations bound the loop; reaching the bound is
+// an internal error.
 // A second bound is time: a loop still running kLevelLoopNs after its first
 // condition stops with a timeout (far beyond any real run: a 1e8-point
 // hull-dense input takes under a second).
@@ -477,12 +480,15 @@ constexpr unsigned long long kLevelLoopNs = 60ull * 1000000000ull;
 
 // First test of the device-driven level loop: run it only if level 0 left
 // segments for level 1 and raised no fatal error.
-__global__ void k_loop_init(Work w, cudaGraphConditionalHandle h) {
+__global__ void k_loop_init(const Work* __restrict__ wp, cudaGraphConditionalHandle h) {
+  const Work& w = *wp;
   const Ctrl* c = w.ctrl;
   cudaGraphSetConditional(h, (c->k1_segs[1] > 0 && !(c->err & kErrFatal)) ? 1u : 0u);
 }
 
-__global__ void k_level_cond(Work w, cudaGraphConditionalHandle h, long long max_iters) {
+__global__ void k_level_cond(const Work* __restrict__ wp, cudaGraphConditionalHandle h) {
+  const Work& w = *wp;
+  const long long max_iters = (long long)w.N / 2 + 4;
   Ctrl* c = w.ctrl;
   const long long it = ++c->graph_iters;
   const unsigned long long now = global_ns();
@@ -979,7 +985,8 @@ __device__ void make_child(const Work& w, const SegRec& P, int a, int b, int r, 
   }
 }
 
-__global__ void k_k2(Work w, int level) {
+__global__ void k_k2(const Work* __restrict__ wp, int level) {
+  const Work& w = *wp;
   if (fatal(w)) return;
   const int par = level & 1, dstb = level & 1;
   const int nseg = min(*reinterpret_cast<volatile int*>(&w.ctrl->k1_segs[par]), w.capS);
@@ -1318,17 +1325,17 @@ cudaError_t launch_sieve(const Work& w, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, long long max_iters, cudaStream_t st) {
+cudaError_t launch_level_cond(const Work& w, cudaGraphConditionalHandle h, cudaStream_t st) {
   count_launch();
-  k_level_cond<<<1, 1, 0, st>>>(w, h, max_iters);
+  k_level_cond<<<1, 1, 0, st>>>(w.dev, h);
   return cudaGetLastError();
 }
 
 void count_launches(long long k) { count_launch((int)k); }
 
 cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphNode_t* node, const Work& w, cudaGraphConditionalHandle h) {
-  Work wc = w;
-  void* args[2] = {&wc, &h};
+  const Work* wd = w.dev;
+  void* args[2] = {&wd, &h};
   cudaKernelNodeParams p = {};
   p.func = reinterpret_cast<void*>(k_loop_init);
   p.gridDim = dim3(1);
@@ -1341,7 +1348,7 @@ cudaError_t add_loop_init_node(cudaGraph_t g, cudaGraphNode_t* node, const Work&
 
 cudaError_t launch_prologue(const Work& w, int level, cudaStream_t st) {
   count_launch();
-  k_prologue<<<1, 1, 0, st>>>(w, level);
+  k_prologue<<<1, 1, 0, st>>>(w.dev, level);
   return cudaGetLastError();
 }
 
@@ -1412,7 +1419,7 @@ int k1_blocks_per_sm(int ppt) {
 
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st) {
   count_launch();
-  k_k2<<<grid, 256, 0, st>>>(w, level);
+  k_k2<<<grid, 256, 0, st>>>(w.dev, level);
   return cudaGetLastError();
 }
 
@@ -1479,7 +1486,7 @@ cudaError_t launch_map_indices(const int* mout, const int* mid, long long h, int
 
 cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st) {
   count_launch();
-  k_tilemap<<<grid, 256, 0, st>>>(w, par);
+  k_tilemap<<<grid, 256, 0, st>>>(w.dev, par);
   return cudaGetLastError();
 }
 
@@ -1496,7 +1503,7 @@ cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st) {
     attr[dev] = true;
   }
   count_launch();
-  k_k3<<<grid, kK3Threads, k3_smem_bytes(), st>>>(w);
+  k_k3<<<grid, kK3Threads, k3_smem_bytes(), st>>>(w.dev);
   return cudaGetLastError();
 }
 

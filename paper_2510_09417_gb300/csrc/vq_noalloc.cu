@@ -43,6 +43,7 @@ struct DeviceState {
 std::mutex g_mu;
 DeviceState g_dev[64];
 Ctrl g_ctrl_host;  // plain host memory: control words read back each level
+Work g_work_host;  // plain host memory: the source of the Work copy in the scratch
 
 size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -87,6 +88,7 @@ size_t carve(Work& w, unsigned char* base, long long n, long long** scan_tmp) {
   }
   w.k3q = reinterpret_cast<SegRec*>(take(sizeof(SegRec) * w.capQ));
   w.ctrl = reinterpret_cast<Ctrl*>(take(sizeof(Ctrl)));
+  w.dev = reinterpret_cast<const Work*>(take(sizeof(Work)));  // the level loop's kernels read Work there
   w.stats = reinterpret_cast<long long*>(take(sizeof(long long) * 3 * kMaxLevels));
   const long long nwords = (nkeys + 31) / 32;
   const long long nb = (nwords + kK4Words - 1) / kK4Words;
@@ -162,6 +164,8 @@ extern "C" vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t
 
   // the scratch keeps the previous call's contents: clear what the kernels
   // expect to start at zero (control words, counters, the vertex bitmap)
+  g_work_host = w;
+  NA_CHECK(cudaMemcpyAsync(const_cast<Work*>(w.dev), &g_work_host, sizeof(Work), cudaMemcpyHostToDevice, st));
   NA_CHECK(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
   NA_CHECK(cudaMemsetAsync(w.stats, 0, sizeof(long long) * 3 * kMaxLevels, st));
   NA_CHECK(cudaMemsetAsync(w.bitmap, 0, sizeof(unsigned) * ((w.nkeys + 31) / 32 + 1), st));

@@ -80,9 +80,9 @@ cudaError_t launch_one(const Work& w, int level, int tiles, cudaStream_t st) {
   if (grid < 1) grid = 1;
   count_launches(1);
   if (level == 0 && !w.sieve)
-    k_k1w<PPT, WPB, NS, true, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
+    k_k1w<PPT, WPB, NS, true, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w.dev, level, w.tier_dev);
   else
-    k_k1w<PPT, WPB, NS, false, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w, level);
+    k_k1w<PPT, WPB, NS, false, ALLFAST><<<(unsigned)grid, 32 * WPB, C::smem, st>>>(w.dev, level, w.tier_dev);
   return cudaGetLastError();
 }
 

@@ -497,7 +497,9 @@ struct K1W {
 // ALLFAST: every point set of the call is in the FP32 tier's range, so only
 // that path is compiled in (a smaller kernel).
 template <int PPT, int WPB, int NS, bool SRC_INPUT, bool ALLFAST>
-__global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Work w, int level) {
+__global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB))
+    k_k1w(const Work* __restrict__ wp, int level, int tier_dev) {
+  const Work& w = *wp;
   typedef K1Ring<PPT, NS> Ring;
   extern __shared__ __align__(128) unsigned char k1w_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(32 * WPB, (K1W<PPT, WPB, NS>::MINB)) k_k1w(Wor
   // warps are independent from here on: each may leave on its own
   if (fatal(w)) return;
   // launched beside its other instantiation: the device's tier flag picks one
-  if (w.tier_dev && ALLFAST == (*reinterpret_cast<volatile int*>(&w.ctrl->any_slow) != 0)) return;
+  if (tier_dev && ALLFAST == (*reinterpret_cast<volatile int*>(&w.ctrl->any_slow) != 0)) return;
   Ring* R = reinterpret_cast<Ring*>(k1w_smem) + warp;
   const int ntiles = min(*reinterpret_cast<volatile int*>(&w.ctrl->k1_tiles[par]), w.capT);
   const long long gw = (long long)blockIdx.x * WPB + warp, nw = (long long)gridDim.x * WPB;

@@ -32,10 +32,13 @@ using Clock = std::chrono::steady_clock;
 constexpr int kDefaultLanes = 3;
 constexpr int kMaxLanes = 16;
 constexpr size_t kBytesFixed = 1 << 20;  // the budget must at least cover this
+constexpr size_t kDefaultPinned = 8ull << 30;  // pinned staging area (at most the budget)
 
 struct Request {
   uint64_t ticket = 0;
-  std::vector<double> x, y;
+  std::vector<double> x, y;   // pageable copy (when the pinned staging area is full)
+  double* px = nullptr;       // pinned copy: x then y, n doubles each
+  size_t pin_off = 0, pin_len = 0;
   int64_t n = 0;
   Clock::time_point t_submit;
   // result
@@ -97,6 +100,10 @@ struct vq_server {
   bool stop = false;
   std::vector<Lane*> lanes;
   cudaMemPool_t pool = nullptr;
+  // pinned staging of submitted points (under mu): free extents offset -> bytes
+  char* pinned = nullptr;
+  size_t pinned_cap = 0;
+  vq::Extents pin_free;
   // admission state (under mu)
   long long resident = 0;  // requests admitted and not finished
   size_t used = 0;         // device bytes of the admitted batches
@@ -151,12 +158,12 @@ static vq_status run_batch(vq_server* s, Lane* L, const std::vector<Request*>& b
   vq_status st = VQ_OK;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < ns && e == cudaSuccess; i++) {
-    if (batch[i]->n == 0) continue;
-    e = cudaMemcpyAsync(dx + offs[i], batch[i]->x.data(), sizeof(double) * batch[i]->n, cudaMemcpyHostToDevice,
-                        L->st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(dy + offs[i], batch[i]->y.data(), sizeof(double) * batch[i]->n, cudaMemcpyHostToDevice,
-                          L->st);
+    const Request* r = batch[i];
+    if (r->n == 0) continue;
+    const double* hx = r->px ? r->px : r->x.data();
+    const double* hy = r->px ? r->px + r->n : r->y.data();
+    e = cudaMemcpyAsync(dx + offs[i], hx, sizeof(double) * r->n, cudaMemcpyHostToDevice, L->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy + offs[i], hy, sizeof(double) * r->n, cudaMemcpyHostToDevice, L->st);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(doff, offs.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, L->st);
@@ -237,6 +244,10 @@ static void lane_main(vq_server* s, Lane* L) {
         r->x.shrink_to_fit();
         r->y.clear();
         r->y.shrink_to_fit();
+        if (r->px) {  // the batch's copies are done (run_batch synchronised its stream)
+          s->pin_free.give(r->pin_off, r->pin_len);
+          r->px = nullptr;
+        }
         r->done = true;
         r->t_done = now;
         s->finished.push_back(r->ticket);
@@ -262,6 +273,8 @@ static void server_free(vq_server* s) {
   s->lanes.clear();
   if (s->pool) cudaMemPoolDestroy(s->pool);
   s->pool = nullptr;
+  if (s->pinned) cudaFreeHost(s->pinned);
+  s->pinned = nullptr;
   for (auto& kv : s->all) delete kv.second;
   s->all.clear();
   delete s;
@@ -296,6 +309,19 @@ vq_status vq_server_create(const vq_server_config* cfg, vq_server** out) {
     unsigned long long keep = (unsigned long long)cfg->mem_budget_bytes;
     cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
+  // pinned staging area for submitted points (device copies from it run at
+  // the link's speed and asynchronously); without it, pageable copies
+  if (st == VQ_OK) {
+    size_t cap = cfg->pinned_bytes ? cfg->pinned_bytes : std::min<size_t>(cfg->mem_budget_bytes, kDefaultPinned);
+    cap &= ~size_t(255);
+    if (cap >= 256 && cudaMallocHost(&s->pinned, cap) == cudaSuccess) {
+      s->pinned_cap = cap;
+      s->pin_free.give(0, cap);
+    } else {
+      cudaGetLastError();
+      s->pinned = nullptr;
+    }
+  }
   for (int i = 0; i < s->nlanes && st == VQ_OK; i++) {
     Lane* L = new Lane();
     L->s = s;
@@ -326,9 +352,26 @@ vq_status vq_server_submit(vq_server* s, const double* x_host, const double* y_h
   if (batch_layout(n, 1).total + kBytesFixed > s->cfg.mem_budget_bytes) return VQ_ERR_BUDGET;
   Request* r = new Request();
   r->n = n;
-  r->x.assign(x_host, x_host + n);
-  r->y.assign(y_host, y_host + n);
   r->t_submit = t0;
+  // the points go to the pinned staging area when it has room, else to
+  // pageable memory
+  size_t off = 0;
+  const size_t bytes = (sizeof(double) * 2 * (size_t)n + 255) & ~size_t(255);
+  bool pinned = false;
+  if (n > 0 && s->pinned) {
+    std::lock_guard<std::mutex> g(s->mu);
+    pinned = s->pin_free.take(bytes, &off);
+  }
+  if (pinned) {
+    r->px = reinterpret_cast<double*>(s->pinned + off);
+    r->pin_off = off;
+    r->pin_len = bytes;
+    memcpy(r->px, x_host, sizeof(double) * (size_t)n);
+    memcpy(r->px + n, y_host, sizeof(double) * (size_t)n);
+  } else {
+    r->x.assign(x_host, x_host + n);
+    r->y.assign(y_host, y_host + n);
+  }
   {
     std::lock_guard<std::mutex> g(s->mu);
     r->ticket = s->next_ticket++;

@@ -275,7 +275,8 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
 // endpoints a, b into shared memory, the slot of its known farthest point,
 // then the rounds.  Per-level counters are summed in shared memory and added
 // to the call's once per block.
-__global__ void __launch_bounds__(kK3Threads) k_k3(Work w) {
+__global__ void __launch_bounds__(kK3Threads) k_k3(const Work* __restrict__ wp) {
+  const Work& w = *wp;
   extern __shared__ __align__(16) unsigned char k3_raw[];
   K3Smem& M = *reinterpret_cast<K3Smem*>(k3_raw);
   if (fatal(w)) return;

@@ -69,6 +69,7 @@ class ServerConfig(ctypes.Structure):
         ("max_inflight", ctypes.c_int32),
         ("device", ctypes.c_int32),
         ("lanes", ctypes.c_int32),
+        ("pinned_bytes", ctypes.c_size_t),
     ]
 
 
@@ -348,9 +349,10 @@ def vq_profile_read(reset: bool = False) -> dict:
 class Server:
     """vq_server_*: hull requests admitted against a device-memory budget."""
 
-    def __init__(self, mem_budget_bytes: int, max_inflight: int = 64, device: int = 0, lanes: int = 0):
+    def __init__(self, mem_budget_bytes: int, max_inflight: int = 64, device: int = 0, lanes: int = 0,
+                 pinned_bytes: int = 0):
         self._lib = load()
-        cfg = ServerConfig(mem_budget_bytes, max_inflight, device, lanes)
+        cfg = ServerConfig(mem_budget_bytes, max_inflight, device, lanes, pinned_bytes)
         h = ctypes.c_void_p()
         _check(self._lib.vq_server_create(ctypes.byref(cfg), ctypes.byref(h)), "vq_server_create")
         self._h = h

@@ -27,5 +27,18 @@ int main() {
   // with it, one byte less leaves room for the first only
   run("reserve_fits", q, 4, 0, 5000, 64, 5000 + 68 * 300 + 2000 + 4096, 4096);
   run("reserve_short", q, 4, 0, 5000, 64, 5000 + 68 * 300 + 2000 + 4095, 4096);
+  // pinned staging extents: first fit, merging on return
+  vq::Extents e;
+  e.give(0, 1000);
+  size_t a = 0, b = 0, c = 0, d = 0;
+  const bool ta = e.take(300, &a), tb = e.take(300, &b), tc = e.take(300, &c), td = e.take(300, &d);
+  std::printf("ext_take %d %d %d %d %zu %zu %zu %zu\n", ta, tb, tc, td, a, b, c, e.largest());
+  e.give(b, 300);  // a hole in the middle
+  size_t f = 0;
+  const bool tf = e.take(301, &f);
+  std::printf("ext_hole %d %zu %zu\n", tf, e.extents(), e.largest());
+  e.give(a, 300);
+  e.give(c, 300);  // all free again: one extent
+  std::printf("ext_merge %zu %zu\n", e.extents(), e.largest());
   return 0;
 }

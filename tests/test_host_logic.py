@@ -167,10 +167,11 @@ def test_strictly_right_of_every_edge_means_strictly_inside():
 
 
 def test_server_admission_policy(tmp_path):
-    """The serving handle's admission (vq_admit.h, host code): the longest
-    FIFO prefix within the free request slots and the memory budget (the
-    server's fixed reserve included), nothing when the head does not fit.
-    Compiled with the host compiler."""
+    """The serving handle's host policies (vq_admit.h): admission (the
+    longest FIFO prefix within the free request slots and the memory budget,
+    the server's fixed reserve included; nothing when the head does not fit)
+    and the pinned staging area's first-fit extents.  Compiled with the host
+    compiler."""
     import os
     import shutil
     import subprocess
@@ -192,3 +193,9 @@ def test_server_admission_policy(tmp_path):
     assert got["empty"] == (0, 0, 0)
     assert got["reserve_fits"] == (2, 300, 68 * 300 + 2000)
     assert got["reserve_short"] == (1, 100, 68 * 100 + 1000)
+    # pinned staging extents: three of 300 fit in 1000 (first fit: 0, 300,
+    # 600), a fourth does not; a freed hole of 300 cannot hold 301; returning
+    # everything merges into one extent of 1000
+    assert got["ext_take"] == (1, 1, 1, 0, 0, 300, 600, 100)
+    assert got["ext_hole"] == (0, 2, 300)
+    assert got["ext_merge"] == (1, 1000)
