@@ -112,8 +112,9 @@ def parse():
                     help="points per workload for the CPU-oracle baseline")
     ap.add_argument("--ppt", type=int, default=0, help="tuning: points per lane of the partition kernel")
     ap.add_argument("--small-max", type=int, default=0, help="tuning: small-segment threshold")
-    ap.add_argument("--autotune", action="store_true",
-                    help="pick the tuning knobs with vq_autotune on the square workload before timing")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default knobs (by default vq_autotune picks them on the square "
+                         "workload before timing)")
     ap.add_argument("--energy-seconds", type=float, default=3.0,
                     help="seconds of back-to-back steps for the energy figure (0: off)")
     ap.add_argument("--no-batched", action="store_true")
@@ -535,7 +536,7 @@ def main():
     outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in dev]
     stream = torch.cuda.current_stream()
     tuned = None
-    if args.autotune:
+    if not args.no_autotune and not (args.ppt or args.small_max):
         cfg, tms = vq.vq_autotune(dev[0][0], dev[0][1], reps=2, stream=stream)
         tuned = {"autotuned_on": "square workload", "median_ms": tms}
 

@@ -404,6 +404,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   // call; h_work is not rewritten before the call's final synchronisation)
   w.dev = c.d_work;
   w.tier_dev = 0;
+  w.key_local_clear = nsets == 1 ? 1 : 0;  // one set: the finalize clears just the words its keys reach
   *c.h_work = w;
   VQ_CHECK(cudaMemcpyAsync(c.d_work, c.h_work, sizeof(Work), cudaMemcpyHostToDevice, st));
 
@@ -412,7 +413,8 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   VQ_CHECK(tm.begin(kKindOther));
   VQ_CHECK(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
   VQ_CHECK(cudaMemsetAsync(w.stats, 0, sizeof(long long) * 3 * kMaxLevels, st));
-  VQ_CHECK(cudaMemsetAsync(w.bitmap, 0, sizeof(unsigned) * ((nkeys + 31) / 32 + 1), st));
+  if (!w.key_local_clear)
+    VQ_CHECK(cudaMemsetAsync(w.bitmap, 0, sizeof(unsigned) * ((nkeys + 31) / 32 + 1), st));
   VQ_CHECK(launch_seed(w, st));
   VQ_CHECK(scan_exclusive_i32(w.k0_tile_start, (long long)nsets + 1, reinterpret_cast<int*>(scan_tmp), st));
   VQ_CHECK(tm.end());

@@ -76,6 +76,8 @@ struct Ctrl {
   long long graph_iters;    // device-driven level loop: iterations of its body (two levels each)
   int live_levels;          // levels >= 1 that started with at least one big segment
   int pad1;
+  long long key_words;      // bitmap words the order pass reads (0: all); a single set's finalize
+                            // sets it to the words its keys can reach and clears them
   unsigned long long loop_t0;  // device-driven level loop: time of its first condition (ns)
 };
 

@@ -70,6 +70,8 @@ struct Work {
   unsigned long long* dirbest;  // per set and sampled direction: packed (score, index) of the extreme
   int* nsurv;                // per set: points the sieve kept (written to buffer 1 from the set's offset)
   int sieve;                 // 1: the pre-filter path (sample, chains, sieve); level 0 reads buffer 1
+  int key_local_clear;       // 1 (one set): the finalize clears the bitmap words the set's keys reach
+                             // (the call then skips clearing the whole bitmap)
 };
 
 // launchers (vq_kernels.cu); all enqueue on `st`

@@ -351,6 +351,19 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_finalize(Work w) {
   __shared__ LexPt s_mn[kK0Threads / kWarp], s_mx[kK0Threads / kWarp];
   __shared__ int s_fl[kK0Threads / kWarp];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (w.nsets == 1 && blockIdx.x == 0 && w.key_local_clear) {
+    // one set: its keys lie in [off + shift, off + shift + len + 1] with
+    // len the points it partitions; the order pass reads just those words,
+    // cleared here (before any emission) instead of the whole bitmap
+    const SetRec S = w.sets[0];
+    const long long len = w.sieve ? min((long long)__ldcg(&w.nsurv[0]), (long long)S.len) : (long long)S.len;
+    long long kw = ((long long)S.off + S.shift + len + 2 + 31) / 32 + 1;
+    const long long all = (w.nkeys + 31) / 32 + 1;
+    if (kw > all) kw = all;
+    for (long long i = threadIdx.x; i < kw; i += blockDim.x) w.bitmap[i] = 0u;
+    if (threadIdx.x == 0) w.ctrl->key_words = kw;
+    __syncthreads();
+  }
   for (int s = blockIdx.x; s < w.nsets; s += gridDim.x) {
     SetRec S = w.sets[s];
     if (S.len == 0) continue;  // uniform across the block
@@ -1061,10 +1074,21 @@ __device__ __forceinline__ int block_excl_scan_256(int v, int* sh, int& total) {
   return r;
 }
 
+// The bitmap words in use: all, or those a single set's finalize cleared.
+__device__ __forceinline__ long long k4_words(long long nwords, const Ctrl* ctrl) {
+  const long long k = *reinterpret_cast<const volatile long long*>(&ctrl->key_words);
+  return k > 0 && k < nwords ? k : nwords;
+}
+
 __global__ void __launch_bounds__(256) k_k4_count(const unsigned* bm, long long nwords, long long* sums,
-                                                  long long nb) {
+                                                  long long nb, const Ctrl* ctrl) {
   __shared__ int sh[24];
   if (blockIdx.x == 0 && threadIdx.x == 0) sums[nb] = 0;  // becomes the total after the scan
+  nwords = k4_words(nwords, ctrl);
+  if ((long long)blockIdx.x * kK4Words >= nwords) {  // beyond the words in use (uniform)
+    if (threadIdx.x == 0) sums[blockIdx.x] = 0;
+    return;
+  }
   const long long w0 = (long long)blockIdx.x * kK4Words + threadIdx.x * 4;
   int c = 0;
 #pragma unroll
@@ -1078,6 +1102,8 @@ __global__ void __launch_bounds__(256) k_k4_count(const unsigned* bm, long long 
 __global__ void __launch_bounds__(256) k_k4_write(const unsigned* bm, long long nwords, const long long* sums,
                                                   const int* slot, int* out, long long cap, Ctrl* ctrl) {
   __shared__ int sh[24];
+  nwords = k4_words(nwords, ctrl);
+  if ((long long)blockIdx.x * kK4Words >= nwords) return;  // uniform
   const long long w0 = (long long)blockIdx.x * kK4Words + threadIdx.x * 4;
   unsigned v[4];
   int c = 0;
@@ -1513,7 +1539,7 @@ cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long 
   const long long nb = (nwords + kK4Words - 1) / kK4Words;
   long long* sums = tmp;  // nb + 1 entries: block prefixes, then the total
   count_launch();
-  k_k4_count<<<(unsigned)nb, 256, 0, st>>>(w.bitmap, nwords, sums, nb);
+  k_k4_count<<<(unsigned)nb, 256, 0, st>>>(w.bitmap, nwords, sums, nb, w.ctrl);
   cudaError_t e = scan_exclusive_i64(sums, nb + 1, tmp + nb + 1, st);
   if (e != cudaSuccess) return e;
   count_launch();

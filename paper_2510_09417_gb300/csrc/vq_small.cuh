@@ -13,6 +13,7 @@ constexpr int kK3Threads = 256;
 constexpr int kK3PPT = kK3Cap / kK3Threads;  // point positions per thread
 constexpr int kK3Frames = kK3Cap / 2;        // open frames hold two points or more
 constexpr unsigned short kNoFrame = 0xffff;
+constexpr int kK3FewCand = 8;  // a frame with at most this many farthest-point candidates: one thread
 
 // Shared memory of one block.  Point slots 0 .. len-1 hold the segment's
 // points, slots kK3Cap and kK3Cap + 1 its endpoints a and b.  Positions are
@@ -141,11 +142,29 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
         if (i == nc - 1 || M.FR[cur][M.cand[i + 1]] != f) M.ce[f] = i + 1;
       }
       __syncthreads();
-      // one warp per frame: each lane keeps the exact best of its share of
-      // the candidates (larger orient, then nearer a, then lower index),
-      // then the warp's butterfly; O(candidates) exact comparisons
+      // a frame with few candidates (the usual case once the keys are
+      // tight): one thread walks them; with many, one warp: each lane keeps
+      // the exact best of its share, then the warp's butterfly.  The order is
+      // larger orient, then nearer a, then lower index; O(candidates) exact
+      // comparisons either way
+      for (int f = tid; f < F; f += kK3Threads) {
+        const int c0 = M.cs[f], c1 = M.ce[f];
+        if (c1 - c0 > kK3FewCand) continue;
+        const double L[4] = {M.X[M.fa[cur][f]], M.Y[M.fa[cur][f]], M.X[M.fb[cur][f]], M.Y[M.fb[cur][f]]};
+        CandT<double> best = cand_none<double>();
+        int bslot = -1;
+        for (int i = c0; i < c1; i++) {
+          const int u = M.P[cur][M.cand[i]];
+          CandT<double> c;
+          c.x = M.X[u]; c.y = M.Y[u]; c.idx = M.I[u];
+          k3_key<FAST>(M, cur, f, c.x, c.y, c.lo, c.hi);
+          if (cand_beats(L, c, best)) { best = c; bslot = u; }
+        }
+        M.fr[f] = (short)bslot;
+      }
       const int lane = tid & 31, warp = tid >> 5;
       for (int f = warp; f < F; f += kK3Threads / kWarp) {
+        if (M.ce[f] - M.cs[f] <= kK3FewCand) continue;  // uniform across the warp
         const double L[4] = {M.X[M.fa[cur][f]], M.Y[M.fa[cur][f]], M.X[M.fb[cur][f]], M.Y[M.fb[cur][f]]};
         CandT<double> best = cand_none<double>();
         for (int i = M.cs[f] + lane; i < M.ce[f]; i += kWarp) {
@@ -275,7 +294,7 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
 // endpoints a, b into shared memory, the slot of its known farthest point,
 // then the rounds.  Per-level counters are summed in shared memory and added
 // to the call's once per block.
-__global__ void __launch_bounds__(kK3Threads) k_k3(const Work* __restrict__ wp) {
+__global__ void __launch_bounds__(kK3Threads, 2) k_k3(const Work* __restrict__ wp) {
   const Work& w = *wp;
   extern __shared__ __align__(16) unsigned char k3_raw[];
   K3Smem& M = *reinterpret_cast<K3Smem*>(k3_raw);
