@@ -197,6 +197,15 @@ typedef struct {
                                 0 (default) 4 warps per block; 1: 8 warps,
                                 a shallower ring; 2: 2 warps, a deeper ring
                                 (per points_per_thread; 0..2)                */
+  int64_t worklist_points;   /* the level loop hands the rest of the
+                                recursion (Alg. 1 on every live segment) to
+                                the persistent worklist at the first level
+                                whose segments hold at most this many points
+                                (default 4,194,304); there a child segment
+                                starts as soon as its parent's last
+                                partition task is done, with no per-level
+                                launches.  0: the level loop to the end.
+                                The hull is the same either way.            */
 } vq_config;
 
 vq_status vq_get_config(vq_config* cfg);
@@ -231,6 +240,10 @@ typedef struct {
   double other_ms;           /* scans, tile maps, counter resets              */
   int64_t graph_launches;    /* level loops run as a device-driven graph      */
   double sample_ms;          /* pre-filter set-up: sampled extremes and chains */
+  double k5_ms;              /* persistent worklist (the recursion below the
+                                level where the level loop hands over)      */
+  int64_t worklist_reruns;   /* calls run again with the level loop alone
+                                after the worklist's queue overflowed       */
 } vq_profile;
 
 vq_status vq_profile_read(vq_profile* out, int32_t reset);

@@ -29,6 +29,7 @@ struct Config {
   int host_loop = 0;
   int prefilter = 1;
   int k1_shape = 0;
+  long long wl_points = 1ll << 22;  // level-loop handover to the persistent worklist (0: never)
 };
 
 static std::mutex g_cfg_mu;
@@ -114,9 +115,14 @@ struct Ctx {
   bool graph_off = false;  // a graph could not be built here: host loop from then on
   std::vector<LevelGraph> graphs;
   unsigned long long graph_clock = 0;
+  // persistent worklist: where its tag array was last time (a new place is
+  // cleared first) and the last epoch published there
+  const unsigned* wl_tag = nullptr;
+  int wl_tag_cap = 0;
+  unsigned wl_epoch = 0;
 };
 
-enum { kKindOther = 0, kKindK0, kKindK1, kKindK2, kKindK3, kKindK4, kKindSample };
+enum { kKindOther = 0, kKindK0, kKindK1, kKindK2, kKindK3, kKindK4, kKindSample, kKindK5 };
 
 // Brackets kernel launches with CUDA events on the call's stream when
 // profiling is on; the times are summed per kernel kind after the call.
@@ -161,6 +167,7 @@ struct Timer {
         case kKindK3: c.prof.k3_ms += ms; break;
         case kKindK4: c.prof.k4_ms += ms; break;
         case kKindSample: c.prof.sample_ms += ms; break;
+        case kKindK5: c.prof.k5_ms += ms; break;
         default: c.prof.other_ms += ms; break;
       }
     }
@@ -226,6 +233,32 @@ static size_t layout(Work& w, char* base, long long N, int nsets, long long nkey
     w.sstate[b] = reinterpret_cast<SegState*>(take(sizeof(SegState) * w.capS));
   }
   w.k3q = reinterpret_cast<SegRec*>(take(sizeof(SegRec) * w.capQ));
+  // persistent worklist (not with look-back offsets, whose layout it would
+  // not keep).  At the handover a level holds at most m points; the table
+  // holds the big segments of the rest of the recursion and the queue their
+  // partition tasks and the small segments.  Both bounds are generous, not
+  // certain: an overflow makes the call run again with the level loop alone.
+  w.wl_points = (cfg.wl_points > 0 && !cfg.ordered) ? cfg.wl_points : 0;
+  if (w.wl_points > 0) {
+    const long long m = n < w.wl_points ? n : w.wl_points;
+    const long long ws = 8 * (m / (cfg.small_max + 1)) + 2LL * nsets + 256;
+    const long long wq = 8 * (m / kWlTaskPts) + 3 * ws + nsets + 1024;
+    w.capWS = (int)(ws < (1LL << 30) ? ws : (1LL << 30));
+    w.capWQ = (int)(wq < (1LL << 30) ? wq : (1LL << 30));
+    // test knob: VQ_WL_QUEUE_CAP=k caps the queue at k entries (the
+    // overflow path: the call runs again with the level loop alone)
+    if (const char* e = getenv("VQ_WL_QUEUE_CAP")) {
+      const long long k = atoll(e);
+      if (k > 0 && k < w.capWQ) w.capWQ = (int)k;
+    }
+  } else {
+    w.capWS = 0;
+    w.capWQ = 0;
+  }
+  w.wlq = reinterpret_cast<WlTask*>(take(sizeof(WlTask) * (size_t)w.capWQ));
+  w.wltag = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * (size_t)w.capWQ));
+  w.wlrec = reinterpret_cast<BestRec*>(take(2 * sizeof(BestRec) * (size_t)w.capWQ));
+  w.wlseg = reinterpret_cast<WlSeg*>(take(sizeof(WlSeg) * (size_t)w.capWS));
   w.ctrl = reinterpret_cast<Ctrl*>(take(sizeof(Ctrl)));
   w.stats = reinterpret_cast<long long*>(take(sizeof(long long) * 3 * kMaxLevels));
   return off;
@@ -370,9 +403,10 @@ static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cach
 // shared-memory recursion, which walks one hull vertex per step).
 static vq_status run(Ctx& c, const double* x, const double* y, const long long* offsets, long long n_single,
                      int nsets, long long N, int* out, long long* hull_offsets, long long* h_out,
-                     cudaStream_t st, int small_max_override = 0, int aos = 0) {
+                     cudaStream_t st, int small_max_override = 0, int aos = 0, int wl_off = 0) {
   Config cfg = get_cfg();
   if (small_max_override > 0) cfg.small_max = small_max_override;
+  if (wl_off) cfg.wl_points = 0;
   if (aos) {  // interleaved points are read by the sieve only (the pre-filter path)
     cfg.prefilter = 1;
     cfg.ordered = 0;
@@ -399,6 +433,18 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   w.ordered = cfg.ordered;
   w.k1_shape = cfg.k1_shape;
   c.d_stats = w.stats;
+
+  // the worklist's queue entries are published with the call's epoch; a
+  // tag array in a new place (or an epoch about to wrap) is cleared first
+  if (w.capWQ > 0) {
+    if (c.wl_tag != w.wltag || c.wl_tag_cap != w.capWQ || c.wl_epoch >= 0xfffffff0u) {
+      VQ_CHECK(cudaMemsetAsync(w.wltag, 0, sizeof(unsigned) * (size_t)w.capWQ, st));
+      c.wl_tag = w.wltag;
+      c.wl_tag_cap = w.capWQ;
+      c.wl_epoch = 0;
+    }
+    w.wl_epoch = ++c.wl_epoch;
+  }
 
   // the level loop's kernels read Work from device memory (one copy per
   // call; h_work is not rewritten before the call's final synchronisation)
@@ -496,7 +542,8 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
       }
     }
   }
-  c.last_levels = levels_run;
+  // the rest of the recursion, when a level handed it over
+  if (w.capWQ > 0) VQ_TIMED(tm, kKindK5, launch_worklist(w, st));
   VQ_TIMED(tm, kKindK4, launch_order(w, out, hull_offsets, &w.ctrl->total, scan_tmp, st));
   VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   VQ_CHECK(cudaStreamSynchronize(st));
@@ -508,6 +555,8 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
     c.prof.k1_launches += 2 * iters;
     c.prof.graph_launches++;
   }
+  if (c.h_ctrl->wl_on && c.h_ctrl->wl_maxlevel > levels_run) levels_run = c.h_ctrl->wl_maxlevel;
+  c.last_levels = levels_run;
   c.prof.calls++;
   c.prof.levels += levels_run;
   c.prof.launches += kernels_launched() - launches0;
@@ -530,9 +579,40 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
             k[0], k[1], k[2], k[3], k[4], k[5], k[6]);
   }
 #endif
+#ifdef VQ_WL_PROFILE
+  if (c.h_ctrl->wl_on) {
+    const unsigned long long* q = c.h_ctrl->k1prof;
+    const unsigned long long t_init = ~q[10], t_start = ~q[6], t_end = q[7];
+    fprintf(stderr,
+            "vqhull wlprof tiles=%llu small=%llu small_pts=%llu wait_ns=%llu tile_ns=%llu small_ns=%llu "
+            "finish_ns=%llu max_small_ns=%llu max_tile_ns=%llu init_to_start_ns=%lld span_ns=%lld "
+            "segs=%d tail=%d\n",
+            q[0], q[1], q[11], q[2], q[3], q[4], q[5], q[8], q[9], (long long)(t_start - t_init),
+            (long long)(t_end - t_start), c.h_ctrl->wl_nseg, (int)(c.h_ctrl->wl_tp >> 32));
+    if (const char* tp = getenv("VQ_WL_TRACE")) wl_trace_dump(tp);
+    unsigned long long tc[4];
+    wl_tier_calls(tc);
+    fprintf(stderr,
+            "vqhull wlprof fp64_filter_calls=%llu exact_calls=%llu classify_exact=%llu beats_exact=%llu (kernels of "
+            "vq_kernels.cu)\n",
+            tc[0], tc[1], tc[2], tc[3]);
+    const unsigned long long* g = c.h_ctrl->k2prof;
+    fprintf(stderr, "vqhull wlprof record ns: merge0=%llu merge1=%llu cursor=%llu multi_lane_merges=%llu\n", g[0],
+            g[1], g[2], g[3]);
+    const unsigned long long* f = c.h_ctrl->k3prof;
+    fprintf(stderr,
+            "vqhull wlprof tile phases ns: seg=%llu classify=%llu (loads=%llu tiers=%llu) sync=%llu record=%llu "
+            "store=%llu ticket=%llu\n",
+            f[0], f[1], f[6], f[7], f[2], f[3], f[4], f[5]);
+  }
+#endif
   if (c.h_ctrl->dbg_site)
     fprintf(stderr, "vqhull: bounds check %d failed (value %lld), level loop ran %d levels\n", c.h_ctrl->dbg_site,
             c.h_ctrl->dbg_val, levels_run);
+  if ((err & kErrWorklistFull) && !wl_off) {  // the worklist overflowed: the level loop alone
+    c.prof.worklist_reruns++;
+    return run(c, x, y, offsets, n_single, nsets, N, out, hull_offsets, h_out, st, small_max_override, aos, 1);
+  }
   if (h_out) *h_out = c.h_ctrl->total;
   if (err & kErrBadOffsets) return VQ_ERR_INVALID_ARG;
   if (err & kErrTimeout) return VQ_ERR_TIMEOUT;
@@ -993,6 +1073,7 @@ vq_status vq_get_config(vq_config* cfg) {
   cfg->host_loop = c.host_loop;
   cfg->prefilter = c.prefilter;
   cfg->k1_shape = c.k1_shape;
+  cfg->worklist_points = c.wl_points;
   return VQ_OK;
 }
 
@@ -1004,6 +1085,7 @@ vq_status vq_set_config(const vq_config* cfg) {
   if (cfg->k1_blocks_per_sm < 0 || cfg->k1_blocks_per_sm > 32) return VQ_ERR_INVALID_ARG;
   if (cfg->timeout_ns <= 0) return VQ_ERR_INVALID_ARG;
   if (cfg->k1_shape < 0 || cfg->k1_shape > 2) return VQ_ERR_INVALID_ARG;
+  if (cfg->worklist_points < 0) return VQ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(g_cfg_mu);
   g_cfg.ppt = cfg->points_per_thread;
   g_cfg.small_max = cfg->small_max;
@@ -1015,6 +1097,7 @@ vq_status vq_set_config(const vq_config* cfg) {
   g_cfg.host_loop = cfg->host_loop ? 1 : 0;
   g_cfg.prefilter = cfg->prefilter ? 1 : 0;
   g_cfg.k1_shape = cfg->k1_shape;
+  g_cfg.wl_points = cfg->worklist_points;
   return VQ_OK;
 }
 

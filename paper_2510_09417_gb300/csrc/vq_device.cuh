@@ -32,7 +32,9 @@ constexpr unsigned kErrNonfinite = 2u;
 constexpr unsigned kErrCapacity = 4u;
 constexpr unsigned kErrInternal = 8u;
 constexpr unsigned kErrBadOffsets = 16u;
-constexpr unsigned kErrFatal = kErrTimeout | kErrCapacity | kErrInternal | kErrBadOffsets;
+constexpr unsigned kErrWorklistFull = 32u;  // the worklist's queue or segment table overflowed: the call
+                                            // is run again with the level loop alone
+constexpr unsigned kErrFatal = kErrTimeout | kErrCapacity | kErrInternal | kErrBadOffsets | kErrWorklistFull;
 
 // segment flags
 constexpr int kSegFast = 1;       // FP32 tier allowed (all |coords| < 2^40)
@@ -79,6 +81,24 @@ struct Ctrl {
   long long key_words;      // bitmap words the order pass reads (0: all); a single set's finalize
                             // sets it to the words its keys can reach and clears them
   unsigned long long loop_t0;  // device-driven level loop: time of its first condition (ns)
+  // persistent worklist (taken over from the level loop once a level is
+  // small).  The counters its blocks update per task or read while they
+  // wait sit in cache lines of their own.
+  // queue entries reserved by producers (high 32 bits) and tasks queued or
+  // running (low 32 bits; 0: the recursion is done), in one word so that a
+  // push is one atomic
+  alignas(128) unsigned long long wl_tp;
+  int wl_pad0[30];
+  int wl_head;              // next queue entry a block claims
+  int wl_pad1[31];
+  int wl_nseg;              // worklist segment slots in use
+  int wl_pad3[31];
+  int wl_on;                // 1: the level loop handed its segments over
+  int wl_par;               // parity of the handed-over level (its segments are segs[wl_par])
+  int wl_nbig;              // handed-over big segments
+  int wl_nsmall;            // handed-over small segments (the small-segment queue)
+  int wl_maxlevel;          // deepest level the worklist reached, plus one
+  int wl_pad4[27];
 };
 
 // A live segment: points off .. off+len-1 of its source buffer, hull edge
@@ -102,6 +122,32 @@ struct SegGeom {
   float o1x, o1y, o2x, o2y;  // origins: truncated a and r (same conversion as points)
   float d1x, d1y, d2x, d2y;  // rounded r-a and b-r
   float k1, c1, k2, c2;      // error bound: E = k*(|ux~|+|uy~|) + c + 2^-22 |d~|
+};
+
+// Persistent worklist.  A big segment (more than small_max points) lives in
+// a slot of the segment table while its partition tasks run: each task
+// classifies and compacts up to kWlTaskPts of its points and leaves the
+// farthest point per child among them in a record; the task that
+// completes the segment (ticket ndone) reduces the records, emits r and
+// pushes the children.
+struct alignas(16) WlSeg {
+  SegRec R;
+  SegGeom G;
+  unsigned long long cursor;  // children's counts (left << 32 | right), as SegState::cursor
+  int ndone;                  // finished tasks
+  int ntasks;                 // tasks of the segment
+  int t0;                     // queue index of its first task (its tasks are t0 .. t0+ntasks-1)
+  int pad[3];
+};
+// A queue entry: a partition task (seg >= 0: points begin .. begin+count-1
+// of segment slot seg) or a small segment (seg < 0: R, finished whole).
+// Entry i is ready when its tag equals the call's epoch.
+struct alignas(16) WlTask {
+  SegRec R;
+  int seg;
+  int begin;
+  int count;
+  int pad;
 };
 
 struct SetRec {
@@ -211,6 +257,19 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -323,9 +382,19 @@ constexpr double kCcwErr = (3.0 + 16.0 * kEps) * kEps;
 
 // sign of (p1-p0) x (q1-q0) if the filter settles it (*sure = true).
 // Also returns the rounded value and its error bound.
+// Profiling builds (VQ_WL_PROFILE): calls of the FP64 filter and of the
+// exact expansions, per translation unit.
+#ifdef VQ_WL_PROFILE
+__device__ unsigned long long g_vq_tier_calls[4];
+#define VQ_COUNT_TIER(i) atomicAdd(&g_vq_tier_calls[i], 1ull)
+#else
+#define VQ_COUNT_TIER(i)
+#endif
+
 __device__ __forceinline__ int cross_f64(double p0x, double p0y, double p1x, double p1y, double q0x,
                                          double q0y, double q1x, double q1y, double& det,
                                          double& bound, bool& sure) {
+  VQ_COUNT_TIER(0);
   const double t1 = __dmul_rn(__dsub_rn(p1x, p0x), __dsub_rn(q1y, q0y));
   const double t2 = __dmul_rn(__dsub_rn(p1y, p0y), __dsub_rn(q1x, q0x));
   det = __dsub_rn(t1, t2);
@@ -363,8 +432,10 @@ __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e
 
 // sign( sum_k sg_k a_k b_k ), n <= 8.  Rare path: loops are kept rolled and
 // the expansion lives in local memory.  Like every helper here it is
-// inlined: the kernels make no device-function calls.
+// inlined: the kernels make no device-function calls (calls measured
+// slower, through their stack traffic, than the larger inlined code).
 static __device__ __forceinline__ int exact_sum_sign(int n, const double* a, const double* b, const int* sg) {
+  VQ_COUNT_TIER(1);
   double e[16];
   int m = 0;
 #pragma unroll 1
@@ -441,6 +512,7 @@ struct CandT {
 static __device__ __forceinline__ bool beats_exact(double ox, double oy, double ex, double ey, double ux, double uy, int ui,
                                          double vx, double vy, int vi) {
   if (ux == vx && uy == vy) return ui < vi;  // coincident: cross and dot are exactly 0
+  VQ_COUNT_TIER(3);
   double det, bound;
   bool sure;
   int c = cross_f64(ox, oy, ex, ey, vx, vy, ux, uy, det, bound, sure);
@@ -724,12 +796,16 @@ __device__ __forceinline__ int classify_filter(const SegGeom& g, const LineF&, c
   return s2 > 0 ? 2 : 0;
 }
 
-// Exact classification (tiers 2 and 3).  A point coincident with r (r
-// itself is in its segment's set) has orient exactly 0 against both lines:
-// it is discarded without the expansions, which the FP64 filter cannot
-// avoid for an exact zero (about 33K cycles per call on GB300).
+// Exact classification (tiers 2 and 3).  A point coincident with r, a or b
+// has orient exactly 0 against the child line through that point, and the
+// sign against the other line is fixed by the segment (r strictly left of
+// a->b, so orient(r, b, a) = -orient(a, b, r) < 0 and orient(a, r, b) < 0;
+// the level-0 segment p->p through q has both orients 0): such a point is
+// discarded without the expansions, which the FP64 filter cannot avoid for
+// an exact zero (about 33K cycles per call on GB300).
 __device__ __forceinline__ int classify_exact(const SegGeom* g, double ux, double uy) {
-  if (ux == g->rx && uy == g->ry) return 0;
+  if ((ux == g->rx && uy == g->ry) || (ux == g->ax && uy == g->ay) || (ux == g->bx && uy == g->by)) return 0;
+  VQ_COUNT_TIER(2);
   if (orient_sign_slow(g->ax, g->ay, g->rx, g->ry, ux, uy) > 0) return 1;
   if (orient_sign_slow(g->rx, g->ry, g->bx, g->by, ux, uy) > 0) return 2;
   return 0;

@@ -19,6 +19,8 @@ constexpr int kSampleEvery = 16;    // kSampleEvery-th extreme-pass tile of a se
 constexpr int kSvWarps = 8;         // sieve: warps per block
 constexpr int kSvMaxBlocks = 4096;  // sieve: most blocks (its partials: one per block and set)
 constexpr int kK3Cap = 1024;        // points per segment in the small-segment kernel (one block each)
+constexpr int kWlPPT = 8;           // worklist partition task: points per thread (256 threads)
+constexpr int kWlTaskPts = 256 * kWlPPT;  // points per worklist partition task
 constexpr int kK3StatLevels = 64;  // levels whose counters the small-segment kernel sums per block
 constexpr int kK4Words = 1024;      // bitmap words per ordering block (256 threads x 4)
 constexpr int kFillTiles = 1024;    // tiles per tile-map fill job
@@ -72,6 +74,16 @@ struct Work {
   int sieve;                 // 1: the pre-filter path (sample, chains, sieve); level 0 reads buffer 1
   int key_local_clear;       // 1 (one set): the finalize clears the bitmap words the set's keys reach
                              // (the call then skips clearing the whole bitmap)
+  // persistent worklist: the level loop hands over at the first level whose
+  // tiles hold at most wl_points points (0: never)
+  long long wl_points;
+  WlTask* wlq;               // queue entries
+  unsigned* wltag;           // per entry: the epoch of the call that published it
+  BestRec* wlrec;            // per entry and child: the partition task's farthest point
+  WlSeg* wlseg;              // segment table
+  int capWQ, capWS;          // queue entries, segment slots
+  unsigned wl_epoch;         // this call's tag value (never 0)
+  int pad_wl;
 };
 
 // launchers (vq_kernels.cu); all enqueue on `st`
@@ -94,6 +106,13 @@ cudaError_t launch_k1w(const Work& w, int level, int ppt, int tiles, cudaStream_
 cudaError_t launch_k2(const Work& w, int level, int grid, cudaStream_t st);
 cudaError_t launch_tilemap(const Work& w, int par, int grid, cudaStream_t st);
 cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st);
+// the persistent worklist: the handed-over segments into its queue, then the
+// persistent kernel (both return at once when the level loop kept going)
+cudaError_t launch_worklist(const Work& w, cudaStream_t st);
+#ifdef VQ_WL_PROFILE
+void wl_tier_calls(unsigned long long* out);
+void wl_trace_dump(const char* path);
+#endif
 cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long long* total,
                          long long* tmp, cudaStream_t st);
 // pipelined host path: chunk-hull points into the merge buffers, and merge

@@ -27,6 +27,8 @@
 // inside the right range, so sorting by key is the in-order traversal of
 // Alg. 1's recursion, i.e. the clockwise hull.  p gets key off + shift.
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 
 #include "vq_internal.h"
 #include "vq_common.cuh"
@@ -466,18 +468,34 @@ __device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, c
   }
 }
 
+// Per-level counter reset.  It is also where the level loop hands over to
+// the persistent worklist: when the level's tiles hold at most wl_points
+// points, its big segments (and, at level 0, the small ones queued with
+// them) are recorded for the worklist and the level's counts are set to
+// zero, so that every later kernel of the loop finds nothing to do and the
+// loop stops.
 __global__ void k_prologue(const Work* __restrict__ wp, int level) {
   const Work& w = *wp;
   const int par = level & 1;
-  w.ctrl->k1_ticket = 0;
-  w.ctrl->k1_segs[par ^ 1] = 0;
-  w.ctrl->k1_tiles[par ^ 1] = 0;
-  w.ctrl->fill_jobs[par ^ 1] = 0;
-  if (level > 0) {
-    w.ctrl->k3_count = 0;
-    if (w.ctrl->k1_segs[par] > 0) w.ctrl->live_levels++;
+  Ctrl* c = w.ctrl;
+  c->k1_ticket = 0;
+  c->k1_segs[par ^ 1] = 0;
+  c->k1_tiles[par ^ 1] = 0;
+  c->fill_jobs[par ^ 1] = 0;
+  if (level > 0) c->k3_count = 0;
+  if (w.wl_points > 0 && !c->wl_on && !(c->err & kErrFatal) &&
+      (long long)c->k1_tiles[par] * w.tile <= w.wl_points) {
+    c->wl_on = 1;
+    c->wl_par = par;
+    c->wl_nbig = c->k1_segs[par];
+    c->wl_nsmall = c->k3_count;
+    c->wl_maxlevel = level;
+    c->k1_segs[par] = 0;
+    c->k1_tiles[par] = 0;
+    c->k3_count = 0;
   }
-  w.ctrl->level = level;
+  if (level > 0 && c->k1_segs[par] > 0) c->live_levels++;
+  c->level = level;
 }
 
 // Condition of the device-driven level loop: a CUDA graph WHILE node whose
@@ -1043,6 +1061,12 @@ __global__ void k_k2(const Work* __restrict__ wp, int level) {
 #include "vq_small.cuh"
 
 // ---------------------------------------------------------------------------
+// K5: the persistent segment worklist (the recursion below a small level)
+// ---------------------------------------------------------------------------
+
+#include "vq_worklist.cuh"
+
+// ---------------------------------------------------------------------------
 // K4: order the emitted vertices by key (bitmap compaction)
 // ---------------------------------------------------------------------------
 
@@ -1530,6 +1554,88 @@ cudaError_t launch_k3(const Work& w, int grid, cudaStream_t st) {
   }
   count_launch();
   k_k3<<<grid, kK3Threads, k3_smem_bytes(), st>>>(w.dev);
+  return cudaGetLastError();
+}
+
+int wl_smem_bytes() { return (int)sizeof(WlSmem); }
+
+#ifdef VQ_WL_PROFILE
+// Profiling builds: the FP64-filter and exact-expansion call counts of this
+// translation unit's kernels since the last read (then cleared).
+// Profiling builds: the per-task trace of the next worklist launch goes to
+// a device buffer; wl_trace_dump writes it to `path` as text.
+static unsigned long long* g_trace_dev = nullptr;
+void wl_trace_arm(cudaStream_t st) {
+  if (!g_trace_dev) {
+    if (cudaMalloc(&g_trace_dev, sizeof(unsigned long long) * 8 * kWlTraceCap) != cudaSuccess) {
+      g_trace_dev = nullptr;
+      return;
+    }
+    cudaMemcpyToSymbol(g_wl_trace, &g_trace_dev, sizeof g_trace_dev);
+  }
+  const int z = 0;
+  cudaMemcpyToSymbolAsync(g_wl_trace_n, &z, sizeof z, 0, cudaMemcpyHostToDevice, st);
+}
+void wl_trace_dump(const char* path) {
+  int n = 0;
+  cudaMemcpyFromSymbol(&n, g_wl_trace_n, sizeof n);
+  if (n > kWlTraceCap) n = kWlTraceCap;
+  if (!g_trace_dev || n <= 0) return;
+  unsigned long long* h = (unsigned long long*)malloc(sizeof(unsigned long long) * 8 * (size_t)n);
+  if (!h) return;
+  cudaMemcpy(h, g_trace_dev, sizeof(unsigned long long) * 8 * (size_t)n, cudaMemcpyDeviceToHost);
+  FILE* f = fopen(path, "a");
+  if (f) {
+    fprintf(f, "# call\n");
+    for (int i = 0; i < n; i++) {
+      const unsigned long long* e = h + 8 * (size_t)i;
+      fprintf(f, "%llu %llu %llu %llu %llu %lld %llu %llu %llu\n", e[0], e[1], e[2], e[3] >> 32, e[3] & 0xffffffffull,
+              (long long)e[4], e[5] >> 32, e[5] & 0xffffffffull, e[6]);
+    }
+    fclose(f);
+  }
+  free(h);
+}
+
+void wl_tier_calls(unsigned long long* out) {
+  out[0] = out[1] = out[2] = out[3] = 0ull;
+  cudaMemcpyFromSymbol(out, g_vq_tier_calls, sizeof(unsigned long long) * 4);
+  const unsigned long long z[4] = {0ull, 0ull, 0ull, 0ull};
+  cudaMemcpyToSymbol(g_vq_tier_calls, z, sizeof z);
+}
+#endif
+
+cudaError_t launch_worklist(const Work& w, cudaStream_t st) {
+  if (w.capWQ == 0 || w.wl_points <= 0) return cudaSuccess;
+  static int blocks[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!blocks[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_wl, cudaFuncAttributeMaxDynamicSharedMemorySize, wl_smem_bytes());
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wl, kWlThreads, wl_smem_bytes());
+    if (e != cudaSuccess) return e;
+    blocks[dev] = (per_sm > 0 ? per_sm : 1) * device_sms();
+  }
+#ifdef VQ_WL_PROFILE
+  if (const char* e = getenv("VQ_WL_BLOCKS")) {  // profiling builds: another grid
+    const int b = atoi(e);
+    if (b > 0 && b < blocks[dev]) {
+      count_launch(2);
+      k_wl_init<<<1, 256, 0, st>>>(w.dev);
+      k_wl<<<b, kWlThreads, wl_smem_bytes(), st>>>(w.dev);
+      return cudaGetLastError();
+    }
+  }
+#endif
+#ifdef VQ_WL_PROFILE
+  wl_trace_arm(st);
+#endif
+  count_launch(2);
+  k_wl_init<<<1, 256, 0, st>>>(w.dev);
+  k_wl<<<blocks[dev], kWlThreads, wl_smem_bytes(), st>>>(w.dev);
   return cudaGetLastError();
 }
 

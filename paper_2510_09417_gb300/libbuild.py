@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libvqhull.so")
 STAMP = os.path.join(BUILD, "lib.arch")
 SOURCES = ["vq_kernels.cu", "vq_partition.cu", "vq_api.cu", "vq_server.cu", "vq_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("vq_device.cuh", "vq_internal.h", "vq_common.cuh", "vq_partition.cuh",
-                                            "vq_sieve.cuh", "vq_admit.h")] + [
+                                            "vq_sieve.cuh", "vq_small.cuh", "vq_worklist.cuh", "vq_admit.h")] + [
     os.path.join(ROOT, "include", "vqhull.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -30,6 +30,10 @@ if CHECKED:
 # printed to stderr after each call (profiling aid; off by default)
 if os.environ.get("VQ_K1_PROFILE", "") == "1":
     FLAGS = FLAGS + ["-DVQ_K1_PROFILE=1"]
+# VQ_WL_PROFILE=1 adds task counts and time sums to the persistent worklist,
+# printed to stderr after each call (profiling aid; off by default)
+if os.environ.get("VQ_WL_PROFILE", "") == "1":
+    FLAGS = FLAGS + ["-DVQ_WL_PROFILE=1"]
 _lock = threading.Lock()
 
 
@@ -53,7 +57,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         srcs = [os.path.join(CSRC, s) for s in SOURCES]
         # a library built on another machine type (e.g. copied to an Arm
         # host) is rebuilt
-        tag = platform.machine() + ("+checked" if CHECKED else "")
+        tag = platform.machine() + "".join(f for f in (" -DVQ_CHECKED=1", " -DVQ_K1_PROFILE=1", " -DVQ_WL_PROFILE=1")
+                                           if f.strip() in FLAGS)
         same_arch = os.path.exists(STAMP) and open(STAMP).read().strip() == tag
         if not force and same_arch and not _stale(LIB, srcs + HEADERS + [__file__]):
             return LIB

@@ -41,6 +41,7 @@ class Config(ctypes.Structure):
         ("host_loop", ctypes.c_int32),
         ("prefilter", ctypes.c_int32),
         ("k1_shape", ctypes.c_int32),
+        ("worklist_points", ctypes.c_int64),
     ]
 
 
@@ -60,6 +61,8 @@ class Profile(ctypes.Structure):
         ("other_ms", ctypes.c_double),
         ("graph_launches", ctypes.c_int64),
         ("sample_ms", ctypes.c_double),
+        ("k5_ms", ctypes.c_double),
+        ("worklist_reruns", ctypes.c_int64),
     ]
 
 
