@@ -75,6 +75,7 @@ struct LevelGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned long long used = 0;
+  int fixed_kernels = 0;  // kernel nodes outside the loop body (level 0, the first test, the worklist)
 };
 constexpr int kGraphCache = 16;           // graphs kept per device (least recently used goes)
 constexpr int kGraphKernelsPerIter = 13;  // two levels of 6 kernels (two partition tiers), and the condition
@@ -268,7 +269,8 @@ static size_t layout(Work& w, char* base, long long N, int nsets, long long nkey
 static size_t scan_bytes(long long nkeys, int nsets) {
   const long long nwords = (nkeys + 31) / 32;
   const long long nb = (nwords + kK4Words - 1) / kK4Words;
-  const long long a = nb + 1 + scan_tmp_elems(nb + 1);
+  long long a = nb + 1 + scan_tmp_elems(nb + 1);
+  if (a < order_fused_tmp_elems(nkeys)) a = order_fused_tmp_elems(nkeys);
   const long long b = scan_tmp_elems((long long)nsets + 1);
   return align_up(sizeof(long long) * (a > b ? a : b));
 }
@@ -317,20 +319,22 @@ static void graph_free(LevelGraph& g) {
 }
 
 // Returns the instantiated level-loop graph for `w` (captured on first use).
-// The body is two levels, parity 1 then parity 0, followed by the condition
-// kernel; a level whose segment count is zero does nothing in any of its
-// kernels, so the second level of the last iteration may run empty.  Level
-// numbers passed to the kernels matter only for their parity and for
-// level > 0 (the level-0 kernels read the caller's arrays and run before the
-// graph).  The partition kernel gets its persistent grid: it reads the
+// It holds everything after the level-0 segments are made: the level-0
+// tile map and level 0 (prologue, partition, finalize, next tile map,
+// finisher), then a WHILE node whose body is two levels, parity 1 then
+// parity 0, followed by the condition kernel, then (when the worklist is
+// on) the worklist's set-up and persistent kernels.  A level whose segment
+// count is zero does nothing in any of its kernels, so the second level of
+// the last iteration may run empty, and after a handover every level
+// kernel finds nothing to do.  All kernels read the call's Work from
+// device memory, so the graph depends only on what shapes its launches
+// (the key).  The partition kernel gets its persistent grid: it reads the
 // level's tile count from the control block.
 // With cached_only set, returns VQ_OK and *out = nullptr when no graph for
 // `w` is cached yet.
 static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cached_only, cudaGraphExec_t* out) {
   *out = nullptr;
-  // the kernels read the call's Work from c.d_work: the graph depends only
-  // on what shapes its launches (points per lane, block shape, SM count)
-  const int kv[3] = {cfg.ppt, cfg.k1_shape, c.sms};
+  const int kv[5] = {cfg.ppt, cfg.k1_shape, c.sms, w.sieve, w.capWQ > 0 ? 1 : 0};
   std::vector<unsigned char> key(sizeof kv);
   memcpy(key.data(), kv, sizeof kv);
   for (LevelGraph& g : c.graphs)
@@ -344,14 +348,43 @@ static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cach
   LevelGraph g;
   g.key = key;
   VQ_CHECK(cudaGraphCreate(&g.graph, 0));
+  const long long before = kernels_launched();
+  cudaStream_t gs = c.gstream;
+  cudaError_t e = cudaSuccess;
+  // level 0, captured into the graph; its last node is the WHILE node's
+  // first dependency
+  cudaGraphNode_t level0_last = nullptr;
+  {
+    e = cudaStreamBeginCaptureToGraph(gs, g.graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      e = launch_tilemap(w, 0, c.sms * 4, gs);
+      if (e == cudaSuccess) e = launch_prologue(w, 0, gs);
+      if (e == cudaSuccess) e = launch_k1(w, 0, cfg.ppt, INT_MAX / 4, gs);
+      if (e == cudaSuccess) e = launch_k2(w, 0, c.sms * 8, gs);
+      if (e == cudaSuccess) e = launch_tilemap(w, 1, c.sms * 4, gs);
+      if (e == cudaSuccess) e = launch_k3(w, c.sms * 2, gs);
+      if (e == cudaSuccess) {
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(gs, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+        if (e == cudaSuccess && ndeps == 1) level0_last = deps[0];
+        else if (e == cudaSuccess) e = cudaErrorInvalidValue;
+      }
+      cudaGraph_t captured = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(gs, &captured);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
   // the loop's condition starts at 0 on every launch; a kernel node ahead
   // of the WHILE node sets it from level 0's result, and the body's last
   // kernel sets it for the next iteration
   cudaGraphConditionalHandle h;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g.graph, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g.graph, 0, cudaGraphCondAssignDefault);
   cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};  // the rest zero
   cudaGraphNode_t init_node, node;
   if (e == cudaSuccess) e = add_loop_init_node(g.graph, &init_node, w, h);
+  if (e == cudaSuccess) e = cudaGraphAddDependencies(g.graph, &level0_last, &init_node, nullptr, 1);
   if (e == cudaSuccess) {
     p.conditional.handle = h;
     p.conditional.type = cudaGraphCondTypeWhile;
@@ -360,10 +393,8 @@ static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cach
   }
   if (e == cudaSuccess) {
     cudaGraph_t body = p.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(c.gstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    e = cudaStreamBeginCaptureToGraph(gs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      const long long before = kernels_launched();
-      cudaStream_t gs = c.gstream;
       for (int level = 1; level <= 2 && e == cudaSuccess; level++) {
         if (e == cudaSuccess) e = launch_prologue(w, level, gs);
         if (e == cudaSuccess) e = launch_k1(w, level, cfg.ppt, INT_MAX / 4, gs);
@@ -375,9 +406,20 @@ static vq_status level_graph(Ctx& c, const Work& w, const Config& cfg, bool cach
       cudaGraph_t captured = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(gs, &captured);
       if (e == cudaSuccess) e = e2;
-      count_launches(before - kernels_launched());  // capturing launches nothing
     }
   }
+  // the rest of the recursion when a level handed it over
+  if (e == cudaSuccess && w.capWQ > 0) {
+    e = cudaStreamBeginCaptureToGraph(gs, g.graph, &node, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      e = launch_worklist(w, gs);
+      cudaGraph_t captured = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(gs, &captured);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  g.fixed_kernels = (int)(kernels_launched() - before) - kGraphKernelsPerIter + 1;  // and the first test
+  count_launches(before - kernels_launched());  // capturing launches nothing
   if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -457,16 +499,19 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   const long long launches0 = kernels_launched();
   Timer tm(c, st, cfg.profile != 0);
   VQ_CHECK(tm.begin(kKindOther));
-  VQ_CHECK(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
-  VQ_CHECK(cudaMemsetAsync(w.stats, 0, sizeof(long long) * 3 * kMaxLevels, st));
-  if (!w.key_local_clear)
-    VQ_CHECK(cudaMemsetAsync(w.bitmap, 0, sizeof(unsigned) * ((nkeys + 31) / 32 + 1), st));
-  VQ_CHECK(launch_seed(w, st));
-  VQ_CHECK(scan_exclusive_i32(w.k0_tile_start, (long long)nsets + 1, reinterpret_cast<int*>(scan_tmp), st));
-  VQ_CHECK(tm.end());
-  if (w.sieve) {
-    VQ_CHECK(cudaMemsetAsync(w.dirbest, 0, sizeof(unsigned long long) * kPolyDirs * nsets, st));
-    VQ_CHECK(cudaMemsetAsync(w.nsurv, 0, sizeof(int) * nsets, st));
+  if (nsets == 1) {  // one kernel clears the counters and seeds the set
+    VQ_CHECK(launch_seed_single(w, st));
+  } else {
+    VQ_CHECK(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), st));
+    VQ_CHECK(cudaMemsetAsync(w.stats, 0, sizeof(long long) * 3 * kMaxLevels, st));
+    if (!w.key_local_clear)
+      VQ_CHECK(cudaMemsetAsync(w.bitmap, 0, sizeof(unsigned) * ((nkeys + 31) / 32 + 1), st));
+    VQ_CHECK(launch_seed(w, st));
+    VQ_CHECK(scan_exclusive_i32(w.k0_tile_start, (long long)nsets + 1, reinterpret_cast<int*>(scan_tmp), st));
+    if (w.sieve) {
+      VQ_CHECK(cudaMemsetAsync(w.dirbest, 0, sizeof(unsigned long long) * kPolyDirs * nsets, st));
+      VQ_CHECK(cudaMemsetAsync(w.nsurv, 0, sizeof(int) * nsets, st));
+    }
   }
   VQ_CHECK(tm.end());
   if (w.sieve) {  // pre-filter path: sample, chains, sieve (the extreme pass over the kept points)
@@ -483,7 +528,6 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   }
   VQ_CHECK(tm.end());
   VQ_TIMED(tm, kKindOther, launch_k0_finalize(w, st));
-  VQ_TIMED(tm, kKindOther, launch_tilemap(w, 0, c.sms * 4, st));
 
   int level = 0;
   int levels_run = 0;
@@ -492,6 +536,7 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
   // look-back (whose grid is one block per tile)
   const bool device_loop = !cfg.host_loop && !cfg.profile && !cfg.ordered;
   bool graph_ran = false;
+  int graph_fixed = 0;
   cudaGraphExec_t ex = nullptr;
   if (device_loop && !c.graph_off) {
     // the partition kernel's tier is picked on the device, so the call has
@@ -505,17 +550,15 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
     if (!ex) w.tier_dev = 0;
   }
   if (ex) {
-    // level 0 from the host, then every later level inside one graph launch
-    VQ_CHECK(launch_prologue(w, 0, st));
-    VQ_CHECK(launch_k1(w, 0, cfg.ppt, (int)(N / w.tile + nsets + 1), st));
-    c.prof.k1_launches++;
-    VQ_CHECK(launch_k2(w, 0, c.sms * 8, st));
-    VQ_CHECK(launch_tilemap(w, 1, c.sms * 4, st));
-    VQ_CHECK(launch_k3(w, c.sms * 2, st));
+    // level 0, every later level and the worklist in one graph launch
+    for (const LevelGraph& g : c.graphs)
+      if (g.exec == ex) graph_fixed = g.fixed_kernels;
     VQ_CHECK(cudaGraphLaunch(ex, st));
+    c.prof.k1_launches++;
     graph_ran = true;
     levels_run = 1;
   } else {
+    VQ_TIMED(tm, kKindOther, launch_tilemap(w, 0, c.sms * 4, st));
     // which partition kernel: FP32-only unless some set needs the FP64 tier
     VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     VQ_CHECK(cudaStreamSynchronize(st));
@@ -542,16 +585,17 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
       }
     }
   }
-  // the rest of the recursion, when a level handed it over
-  if (w.capWQ > 0) VQ_TIMED(tm, kKindK5, launch_worklist(w, st));
-  VQ_TIMED(tm, kKindK4, launch_order(w, out, hull_offsets, &w.ctrl->total, scan_tmp, st));
+  // the rest of the recursion, when a level handed it over (inside the graph
+  // when the graph ran)
+  if (w.capWQ > 0 && !graph_ran) VQ_TIMED(tm, kKindK5, launch_worklist(w, st));
+  VQ_TIMED(tm, kKindK4, launch_order_fused(w, out, hull_offsets, &w.ctrl->total, scan_tmp, st));
   VQ_CHECK(cudaMemcpyAsync(c.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   VQ_CHECK(cudaStreamSynchronize(st));
   tm.collect();
   if (graph_ran) {
     const long long iters = c.h_ctrl->graph_iters;
     levels_run = 1 + c.h_ctrl->live_levels;
-    count_launches(1 + iters * kGraphKernelsPerIter);  // the loop's first test, then the body
+    count_launches(graph_fixed + iters * kGraphKernelsPerIter);  // level 0, first test, worklist; the body
     c.prof.k1_launches += 2 * iters;
     c.prof.graph_launches++;
   }

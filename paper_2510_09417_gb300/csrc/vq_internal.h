@@ -88,6 +88,8 @@ struct Work {
 
 // launchers (vq_kernels.cu); all enqueue on `st`
 cudaError_t launch_seed(const Work& w, cudaStream_t st);
+// one point set: counters cleared and the set seeded in one kernel
+cudaError_t launch_seed_single(const Work& w, cudaStream_t st);
 cudaError_t launch_k0(const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_k0_finalize(const Work& w, cudaStream_t st);
 // pre-filter path: sampled direction extremes, chains per set, the sieve
@@ -115,6 +117,11 @@ void wl_trace_dump(const char* path);
 #endif
 cudaError_t launch_order(const Work& w, int* out, long long* hull_offsets, long long* total,
                          long long* tmp, cudaStream_t st);
+// the same in one pass (decoupled look-back over bitmap chunks); tmp holds
+// order_fused_tmp_elems(nkeys) entries
+cudaError_t launch_order_fused(const Work& w, int* out, long long* hull_offsets, long long* total,
+                               long long* tmp, cudaStream_t st);
+long long order_fused_tmp_elems(long long nkeys);
 // pipelined host path: chunk-hull points into the merge buffers, and merge
 // indices back to original indices
 cudaError_t launch_gather(const double* x, const double* y, const int* idx, long long m, long long base, double* mx,

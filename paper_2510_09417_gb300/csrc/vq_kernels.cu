@@ -172,6 +172,42 @@ __global__ void k_seed(Work w) {
   w.k0_tile_start[s] = (r.len + kK0Tile - 1) / kK0Tile;
 }
 
+// One point set: the control block, the level counters and (pre-filter
+// path) the set's sampled extremes and survivor count cleared, then the
+// set's record and its extreme-pass tiles [0, tiles) (what k_seed and the
+// scan of k0_tile_start give for one set), in one block.
+__global__ void __launch_bounds__(256) k_seed_single(Work w) {
+  static_assert(sizeof(Ctrl) % sizeof(int4) == 0, "Ctrl is cleared as int4");
+  int4* c4 = reinterpret_cast<int4*>(w.ctrl);
+  for (int i = threadIdx.x; i < (int)(sizeof(Ctrl) / sizeof(int4)); i += blockDim.x) c4[i] = make_int4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < 3 * kMaxLevels; i += blockDim.x) w.stats[i] = 0;
+  if (w.sieve) {
+    for (int i = threadIdx.x; i < kPolyDirs; i += blockDim.x) w.dirbest[i] = 0ull;
+    if (threadIdx.x == 0) w.nsurv[0] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  w.ctrl->nonfinite_set = LLONG_MAX;
+  const long long off = w.offsets ? w.offsets[0] : 0;
+  const long long end = w.offsets ? w.offsets[1] : w.n_single;
+  SetRec r;
+  if (off != 0 || end != w.N) {
+    atomicOr(&w.ctrl->err, kErrBadOffsets);
+    r.off = 0;
+    r.len = 0;
+  } else {
+    r.off = 0;
+    r.len = (int)end;
+  }
+  r.shift = w.key_base ? w.key_base[0] : 0;
+  r.flags = 0;
+  r.p = r.q = -1;
+  r.pad = 0;
+  w.sets[0] = r;
+  w.k0_tile_start[0] = 0;
+  w.k0_tile_start[1] = (r.len + kK0Tile - 1) / kK0Tile;
+}
+
 struct LexPt {
   long long kx, ky;
   int i;
@@ -1157,6 +1193,90 @@ __global__ void __launch_bounds__(256) k_k4_write(const unsigned* bm, long long 
   }
 }
 
+// One-pass ordering: chunks of kK4Words bitmap words, taken in order by a
+// ticket; each chunk counts its set bits, publishes the count, finds its
+// exclusive prefix by decoupled look-back over the chunks before it (their
+// status words: 0 not yet, count << 2 | 1 aggregate, prefix << 2 | 2
+// inclusive), publishes its inclusive prefix and writes its vertices.
+// Only the chunks that hold the words in use are taken.  sums[c] gets
+// chunk c's exclusive prefix and sums[nb] the total (for the per-set
+// offsets); every wait is bounded by timeout_ns.
+__global__ void __launch_bounds__(256) k_k4_fused(const unsigned* bm, long long nwords, unsigned long long* status,
+                                                  unsigned* ticket, long long* sums, long long nb, const int* slot,
+                                                  int* out, long long cap, Ctrl* ctrl, long long* total,
+                                                  long long timeout_ns) {
+  __shared__ int sh[24];
+  __shared__ int s_t;
+  __shared__ long long s_pre;
+  const long long nw = k4_words(nwords, ctrl);
+  const long long nch = (nw + kK4Words - 1) / kK4Words;
+  if (nch == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      *total = 0;
+      sums[nb] = 0;
+    }
+    return;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_t = (int)atomicAdd(ticket, 1u);
+    __syncthreads();
+    const long long t = s_t;
+    if (t >= nch) return;  // uniform
+    const long long w0 = t * kK4Words + threadIdx.x * 4;
+    unsigned v[4];
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      v[q] = (w0 + q < nw) ? bm[w0 + q] : 0u;
+      c += __popc(v[q]);
+    }
+    int cnt;
+    const int pre = block_excl_scan_256(c, sh, cnt);
+    if (threadIdx.x == 0) {
+      long long acc = 0;
+      if (t == 0) {
+        st_release_u64(&status[0], ((unsigned long long)cnt << 2) | 2ull);
+      } else {
+        st_release_u64(&status[t], ((unsigned long long)cnt << 2) | 1ull);
+        const unsigned long long t0 = global_ns();
+        for (long long j = t - 1; j >= 0;) {
+          const unsigned long long sv = ld_acquire_u64(&status[j]);
+          if ((sv & 3ull) == 0ull) {
+            if (global_ns() - t0 > (unsigned long long)timeout_ns) {
+              atomicOr(&ctrl->err, kErrTimeout);
+              break;
+            }
+            continue;
+          }
+          acc += (long long)(sv >> 2);
+          if ((sv & 3ull) == 2ull) break;
+          j--;
+        }
+        st_release_u64(&status[t], ((unsigned long long)(acc + cnt) << 2) | 2ull);
+      }
+      sums[t] = acc;
+      if (t == nch - 1) {
+        *total = acc + cnt;
+        sums[nb] = acc + cnt;
+      }
+      s_pre = acc;
+    }
+    __syncthreads();
+    long long pos = s_pre + pre;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      unsigned m = v[q];
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        if (pos < cap) out[pos] = slot[(w0 + q) * 32 + b];
+        pos++;
+      }
+    }
+    __syncthreads();  // s_t and s_pre are rewritten by the next chunk
+  }
+}
+
 // Rank of a key among the emitted ones (set bits below it), one warp per
 // key: the block prefix plus the bits of the words before it in its block.
 __device__ __forceinline__ long long key_rank_warp(const unsigned* bm, long long nwords, const long long* sums,
@@ -1271,6 +1391,12 @@ cudaError_t scan_exclusive_i64(long long* data, long long n, long long* tmp, cud
 // launchers
 // ---------------------------------------------------------------------------
 
+
+cudaError_t launch_seed_single(const Work& w, cudaStream_t st) {
+  count_launch();
+  k_seed_single<<<1, 256, 0, st>>>(w);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_seed(const Work& w, cudaStream_t st) {
   const int blocks = (w.nsets + 255) / 256;
@@ -1636,6 +1762,37 @@ cudaError_t launch_worklist(const Work& w, cudaStream_t st) {
   count_launch(2);
   k_wl_init<<<1, 256, 0, st>>>(w.dev);
   k_wl<<<blocks[dev], kWlThreads, wl_smem_bytes(), st>>>(w.dev);
+  return cudaGetLastError();
+}
+
+// tmp: status words (nb), the ticket, the chunk prefixes and the total
+// (nb + 1); 2 nb + 3 entries.
+long long order_fused_tmp_elems(long long nkeys) {
+  const long long nb = ((nkeys + 31) / 32 + kK4Words - 1) / kK4Words;
+  return 2 * nb + 3;
+}
+
+cudaError_t launch_order_fused(const Work& w, int* out, long long* hull_offsets, long long* total, long long* tmp,
+                               cudaStream_t st) {
+  const long long nwords = (w.nkeys + 31) >> 5;
+  const long long nb = (nwords + kK4Words - 1) / kK4Words;
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(tmp);
+  unsigned* ticket = reinterpret_cast<unsigned*>(tmp + nb);
+  long long* sums = tmp + nb + 1;
+  cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(long long) * (size_t)(nb + 1), st);
+  if (e != cudaSuccess) return e;
+  long long grid = 2LL * device_sms();
+  if (grid > nb) grid = nb;
+  if (grid < 1) grid = 1;
+  count_launch();
+  k_k4_fused<<<(unsigned)grid, 256, 0, st>>>(w.bitmap, nwords, status, ticket, sums, nb, w.slot, out, (long long)w.N,
+                                             w.ctrl, total, w.timeout_ns);
+  if (hull_offsets) {
+    long long blocks = ((long long)w.nsets + 7) / 8;
+    if (blocks > 1024) blocks = 1024;
+    count_launch();
+    k_k4_offsets<<<(unsigned)blocks, 256, 0, st>>>(w, sums, nb, hull_offsets, nullptr);
+  }
   return cudaGetLastError();
 }
 
