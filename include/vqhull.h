@@ -163,6 +163,16 @@ vq_status vq_hull2d_noalloc(const double* x, const double* y, int64_t n, int32_t
  */
 vq_status vq_debug_orient_f32(const double* tri, int64_t m, int32_t tier, float* d, float* e, void* stream);
 
+/*
+ * Test access to the FP64 -> FP32 rounding that the FP32 tiers use for the
+ * line direction D~ = fl32(fl64(e - o)) and the relative coordinates
+ * T~ = fl32(fl64(u - o)) (IEEE 754 round to nearest, ties to even, done
+ * with integer operations): out[k] = fl32(v[k]) for m device FP64 values.
+ * Synchronises `stream`.  Returns VQ_ERR_INVALID_ARG for m < 0 or null
+ * arrays.
+ */
+vq_status vq_debug_round_f32(const double* v, int64_t m, float* out, void* stream);
+
 /* Tuning knobs (process-wide; take effect on the next call). */
 typedef struct {
   int32_t points_per_thread; /* partition kernel: 4, 8 or 16 points per lane

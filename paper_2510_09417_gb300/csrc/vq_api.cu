@@ -634,12 +634,12 @@ static vq_status run(Ctx& c, const double* x, const double* y, const long long* 
             q[0], q[1], q[11], q[2], q[3], q[4], q[5], q[8], q[9], (long long)(t_start - t_init),
             (long long)(t_end - t_start), c.h_ctrl->wl_nseg, (int)(c.h_ctrl->wl_tp >> 32));
     if (const char* tp = getenv("VQ_WL_TRACE")) wl_trace_dump(tp);
-    unsigned long long tc[4];
+    unsigned long long tc[8];
     wl_tier_calls(tc);
     fprintf(stderr,
-            "vqhull wlprof fp64_filter_calls=%llu exact_calls=%llu classify_exact=%llu beats_exact=%llu (kernels of "
-            "vq_kernels.cu)\n",
-            tc[0], tc[1], tc[2], tc[3]);
+            "vqhull wlprof fp64_filter_calls=%llu exact_calls=%llu classify_exact=%llu beats_exact=%llu "
+            "classify_rel=%llu orient_rel=%llu (kernels of vq_kernels.cu)\n",
+            tc[0], tc[1], tc[2], tc[3], tc[4], tc[5]);
     const unsigned long long* g = c.h_ctrl->k2prof;
     fprintf(stderr, "vqhull wlprof record ns: merge0=%llu merge1=%llu cursor=%llu multi_lane_merges=%llu\n", g[0],
             g[1], g[2], g[3]);
@@ -1142,6 +1142,14 @@ vq_status vq_set_config(const vq_config* cfg) {
   g_cfg.prefilter = cfg->prefilter ? 1 : 0;
   g_cfg.k1_shape = cfg->k1_shape;
   g_cfg.wl_points = cfg->worklist_points;
+  return VQ_OK;
+}
+
+vq_status vq_debug_round_f32(const double* v, int64_t m, float* out, void* stream) {
+  if (m < 0 || (m > 0 && (!v || !out))) return VQ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  VQ_CHECK(launch_debug_round_f32(v, m, out, st));
+  VQ_CHECK(cudaStreamSynchronize(st));
   return VQ_OK;
 }
 

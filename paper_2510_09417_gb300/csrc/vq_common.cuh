@@ -40,6 +40,13 @@ __device__ __forceinline__ void take_best(CandT<K>& b, const double* L, double x
     b.x = x; b.y = y; b.lo = lo; b.hi = hi; b.idx = idx;
   }
 }
+// The same with the line's FP32 constants (the difference tier first).
+__device__ __forceinline__ void take_best(CandT<float>& b, const LineF& Lf, const double* L, double x, double y,
+                                          int idx, float key, float err) {
+  CandT<float> c;
+  c.x = x; c.y = y; c.lo = key_lo(key, err); c.hi = key_hi(key, err); c.idx = idx;
+  if (cand_beats(Lf, L, c, b)) b = c;
+}
 
 template <typename K>
 __device__ __forceinline__ CandT<double> to_double(const CandT<K>& c) {

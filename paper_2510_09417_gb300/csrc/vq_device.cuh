@@ -315,6 +315,46 @@ __device__ __forceinline__ double f2d_exact(float f) {
 __device__ __forceinline__ double widen(float v) { return f2d_exact(v); }
 __device__ __forceinline__ double widen(double v) { return v; }
 
+// FP64 -> FP32 rounded to nearest (ties to even) by integer operations,
+// from the IEEE 754 definition: normal results keep the top 23 fraction
+// bits and round on the 29 dropped ones (a carry moves into the exponent,
+// up to infinity); results below 2^-126 are FP32 subnormals m 2^-149 with m
+// rounded from the full significand; infinities and NaNs keep their class.
+// GB300's FP64 pipe (conversions included) has about 64 cycles of latency;
+// this runs on the integer pipe.
+__device__ __forceinline__ float f32_rn(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffull);
+  const unsigned long long f = b & 0xfffffffffffffull;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (f ? 0x00400000u : 0u));
+  const int ef = e - 896;  // FP32 biased exponent (1023 - 127)
+  unsigned r;
+  if (ef > 0) {
+    if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+    r = ((unsigned)ef << 23) | (unsigned)(f >> 29);
+    const unsigned rem = (unsigned)(f & 0x1fffffffull);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) r++;  // may carry into the exponent
+  } else {
+    const int sh = 30 - ef;  // value = M 2^(e - 1075), unit 2^-149: M >> (926 - e)
+    if (e == 0 || sh >= 64) return __uint_as_float(sign);  // below half the smallest subnormal
+    const unsigned long long M = f | (1ull << 52);
+    r = (unsigned)(M >> sh);
+    const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (r & 1u))) r++;
+  }
+  return __uint_as_float(sign | r);
+}
+
+// Profiling builds (VQ_WL_PROFILE): calls of the FP64 filter and of the
+// exact expansions, per translation unit.
+#ifdef VQ_WL_PROFILE
+__device__ unsigned long long g_vq_tier_calls[8];
+#define VQ_COUNT_TIER(i) atomicAdd(&g_vq_tier_calls[i], 1ull)
+#else
+#define VQ_COUNT_TIER(i)
+#endif
+
 // ---------------------------------------------------------------------------
 // Tier 1: FP32 orient with a rigorous error bound.
 //
@@ -363,8 +403,9 @@ __device__ __forceinline__ void orient_f32(const LineF& L, float ux, float uy, f
 
 __device__ __forceinline__ void orient_rel(const LineF& L, double ox, double oy, double ux, double uy, float& d,
                                            float& e) {
-  const float tx = __double2float_rn(__dsub_rn(ux, ox));
-  const float ty = __double2float_rn(__dsub_rn(uy, oy));
+  VQ_COUNT_TIER(5);
+  const float tx = f32_rn(__dsub_rn(ux, ox));
+  const float ty = f32_rn(__dsub_rn(uy, oy));
   const float m = __fadd_ru(fabsf(tx), fabsf(ty));
   const float p = __fmul_rn(L.dy, tx);
   d = __fmaf_rn(L.dx, ty, -p);
@@ -382,15 +423,6 @@ constexpr double kCcwErr = (3.0 + 16.0 * kEps) * kEps;
 
 // sign of (p1-p0) x (q1-q0) if the filter settles it (*sure = true).
 // Also returns the rounded value and its error bound.
-// Profiling builds (VQ_WL_PROFILE): calls of the FP64 filter and of the
-// exact expansions, per translation unit.
-#ifdef VQ_WL_PROFILE
-__device__ unsigned long long g_vq_tier_calls[4];
-#define VQ_COUNT_TIER(i) atomicAdd(&g_vq_tier_calls[i], 1ull)
-#else
-#define VQ_COUNT_TIER(i)
-#endif
-
 __device__ __forceinline__ int cross_f64(double p0x, double p0y, double p1x, double p1y, double q0x,
                                          double q0y, double q1x, double q1y, double& det,
                                          double& bound, bool& sure) {
@@ -526,12 +558,45 @@ static __device__ __forceinline__ bool beats_exact(double ox, double oy, double 
 
 // L points at the line's endpoints {ox, oy, ex, ey} (read only when the
 // bounds overlap, so the hot paths keep no FP64 endpoints in registers).
+// Bounds compared without FP64 instructions: FP32 as is, FP64 through
+// their order-preserving integer images (-0 and +0 alike).
+__device__ __forceinline__ bool bound_gt(float a, float b) { return a > b; }
+__device__ __forceinline__ bool bound_gt(double a, double b) { return order_key(a) > order_key(b); }
+
 template <typename K>
 __device__ __forceinline__ bool cand_beats(const double* L, const CandT<K>& u, const CandT<K>& v) {
   if (u.idx < 0) return false;
   if (v.idx < 0) return true;
-  if (u.lo > v.hi) return true;
-  if (v.lo > u.hi) return false;
+  if (bound_gt(u.lo, v.hi)) return true;
+  if (bound_gt(v.lo, u.hi)) return false;
+  return beats_exact(L[0], L[1], L[2], L[3], u.x, u.y, u.idx, v.x, v.y, v.idx);
+}
+
+// Which of u, v is farther to the left of the line L (o -> e), decided in
+// FP32 on their difference: orient(o, e, u) - orient(o, e, v) equals
+// D x T with T = u - v, so the relative tier's evaluation and bound apply
+// with T~ = fl32(fl64(u - v)) in place of fl32(fl64(u - o)).  Returns 1
+// (u farther), -1 (v farther) or 0 (within the bound: a near tie, for the
+// exact tiers).  Candidates near the farthest point are close to each
+// other, so |T| and the bound are small where the keys' own bounds overlap.
+__device__ __forceinline__ int beats_rel(const LineF& L, double ux, double uy, double vx, double vy) {
+  float d, e;
+  orient_rel(L, vx, vy, ux, uy, d, e);
+  return d > e ? 1 : (d < -e ? -1 : 0);
+}
+
+// cand_beats with the line's FP32 constants: bounds, then the difference
+// tier, then the exact tiers.
+template <typename K>
+__device__ __forceinline__ bool cand_beats(const LineF& Lf, const double* L, const CandT<K>& u, const CandT<K>& v) {
+  if (u.idx < 0) return false;
+  if (v.idx < 0) return true;
+  if (bound_gt(u.lo, v.hi)) return true;
+  if (bound_gt(v.lo, u.hi)) return false;
+  if (__double_as_longlong(u.x) == __double_as_longlong(v.x) && __double_as_longlong(u.y) == __double_as_longlong(v.y))
+    return u.idx < v.idx;  // the same point (other equal pairs reach the exact tiers)
+  const int r = beats_rel(Lf, u.x, u.y, v.x, v.y);
+  if (r != 0) return r > 0;
   return beats_exact(L[0], L[1], L[2], L[3], u.x, u.y, u.idx, v.x, v.y, v.idx);
 }
 
@@ -564,6 +629,15 @@ __device__ __forceinline__ CandT<K> warp_best(const double* L, CandT<K> c) {
   }
   return c;
 }
+template <typename K>
+__device__ __forceinline__ CandT<K> warp_best(const LineF& Lf, const double* L, CandT<K> c) {
+#pragma unroll 1
+  for (int m = 16; m >= 1; m >>= 1) {
+    const CandT<K> o = shfl_xor_cand(c, m);
+    if (cand_beats(Lf, L, o, c)) c = o;
+  }
+  return c;
+}
 
 __device__ __forceinline__ float warp_max_f(float v) {
 #pragma unroll
@@ -591,16 +665,18 @@ __device__ inline LineF make_line(double ox, double oy, double ex, double ey) {
   LineF L;
   L.ox = trunc_f32(ox);
   L.oy = trunc_f32(oy);
-  const double dx = __dsub_rn(ex, ox);
-  const double dy = __dsub_rn(ey, oy);
-  L.dx = __double2float_rn(dx);
-  L.dy = __double2float_rn(dy);
+  // D~ = fl32(fl64(e - o)), rounded to nearest (the tiers' derivations)
+  L.dx = f32_rn(__dsub_rn(ex, ox));
+  L.dy = f32_rn(__dsub_rn(ey, oy));
   // rho >= (1 + 2^-22) max |D~|; the rounding of dx, dy in FP64 (2^-53) is
-  // covered by the factor as well
-  const double rho = fmax(fabs((double)L.dx), fabs((double)L.dy)) * (1.0 + 0x1p-21);
-  L.k = __double2float_ru(4.0 * 0x1p-23 * rho);
-  const double mag = fabs(ox) + fabs(oy);
-  L.c = __double2float_ru(4.0 * 0x1p-23 * rho * mag * (1.0 + 0x1p-20) + rho * 0x1p-100 + 0x1p-100);
+  // covered by the factor as well.  Everything below rounds upward in FP32,
+  // so k and c are at least the derivation's values.
+  const float rho = __fmul_ru(fmaxf(fabsf(L.dx), fabsf(L.dy)), 1.0f + 0x1p-21f);
+  L.k = __fmul_ru(rho, 0x1p-21f);  // 4 * 2^-23 rho
+  // mag >= |ox| + |oy|: |w| <= (|w~| + 2^-125)(1 + 2^-22) for the truncation w~
+  const float mag =
+      __fmul_ru(__fadd_ru(__fadd_ru(fabsf(L.ox), fabsf(L.oy)), 0x1p-124f), 1.0f + 0x1p-22f);
+  L.c = __fadd_ru(__fadd_ru(__fmul_ru(__fmul_ru(L.k, mag), 1.0f + 0x1p-20f), __fmul_ru(rho, 0x1p-100f)), 0x1p-100f);
   return L;
 }
 
@@ -858,6 +934,7 @@ __device__ __forceinline__ void line_key_tight(const LineF& L, const double* E, 
 // undecided): 0, 1, 2 as classify_filter, 3 when it is unsure as well.
 __device__ __forceinline__ int classify_rel(const SegGeom& g, const LineF& l1, const LineF& l2, double ux,
                                             double uy, float& key, float& err) {
+  VQ_COUNT_TIER(4);
   float d1, e1;
   orient_rel(l1, g.ax, g.ay, ux, uy, d1, e1);
   if (d1 > e1) { key = d1; err = e1; return 1; }

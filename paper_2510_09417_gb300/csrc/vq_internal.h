@@ -19,7 +19,7 @@ constexpr int kSampleEvery = 16;    // kSampleEvery-th extreme-pass tile of a se
 constexpr int kSvWarps = 8;         // sieve: warps per block
 constexpr int kSvMaxBlocks = 4096;  // sieve: most blocks (its partials: one per block and set)
 constexpr int kK3Cap = 1024;        // points per segment in the small-segment kernel (one block each)
-constexpr int kWlPPT = 8;           // worklist partition task: points per thread (256 threads)
+constexpr int kWlPPT = 4;           // worklist partition task: points per thread (256 threads)
 constexpr int kWlTaskPts = 256 * kWlPPT;  // points per worklist partition task
 constexpr int kK3StatLevels = 64;  // levels whose counters the small-segment kernel sums per block
 constexpr int kK4Words = 1024;      // bitmap words per ordering block (256 threads x 4)
@@ -126,6 +126,7 @@ long long order_fused_tmp_elems(long long nkeys);
 // indices back to original indices
 cudaError_t launch_gather(const double* x, const double* y, const int* idx, long long m, long long base, double* mx,
                           double* my, int* mid, cudaStream_t st);
+cudaError_t launch_debug_round_f32(const double* v, long long m, float* out, cudaStream_t st);
 cudaError_t launch_debug_orient_f32(const double* tri, long long m, int tier, float* d, float* e, cudaStream_t st);
 cudaError_t launch_map_indices(const int* mout, const int* mid, long long h, int* out, cudaStream_t st);
 cudaError_t scan_exclusive_i32(int* data, long long n, int* tmp, cudaStream_t st);

@@ -1615,6 +1615,20 @@ __global__ void k_debug_orient_f32(const double* tri, long long m, int tier, flo
   }
 }
 
+__global__ void k_debug_round_f32(const double* v, long long m, float* out) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x)
+    out[k] = f32_rn(v[k]);
+}
+
+cudaError_t launch_debug_round_f32(const double* v, long long m, float* out, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  long long blocks = (m + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  count_launch();
+  k_debug_round_f32<<<(unsigned)blocks, 256, 0, st>>>(v, m, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_debug_orient_f32(const double* tri, long long m, int tier, float* d, float* e, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   long long blocks = (m + 255) / 256;
@@ -1715,8 +1729,8 @@ void wl_trace_dump(const char* path) {
     fprintf(f, "# call\n");
     for (int i = 0; i < n; i++) {
       const unsigned long long* e = h + 8 * (size_t)i;
-      fprintf(f, "%llu %llu %llu %llu %llu %lld %llu %llu %llu\n", e[0], e[1], e[2], e[3] >> 32, e[3] & 0xffffffffull,
-              (long long)e[4], e[5] >> 32, e[5] & 0xffffffffull, e[6]);
+      fprintf(f, "%llu %llu %llu %llu %llu %lld %llu %llu %llu %llu\n", e[0], e[1], e[2], e[3] >> 32,
+              e[3] & 0xffffffffull, (long long)e[4], e[5] >> 32, e[5] & 0xffffffffull, e[6], e[7]);
     }
     fclose(f);
   }
@@ -1724,9 +1738,9 @@ void wl_trace_dump(const char* path) {
 }
 
 void wl_tier_calls(unsigned long long* out) {
-  out[0] = out[1] = out[2] = out[3] = 0ull;
-  cudaMemcpyFromSymbol(out, g_vq_tier_calls, sizeof(unsigned long long) * 4);
-  const unsigned long long z[4] = {0ull, 0ull, 0ull, 0ull};
+  for (int i = 0; i < 8; i++) out[i] = 0ull;
+  cudaMemcpyFromSymbol(out, g_vq_tier_calls, sizeof(unsigned long long) * 8);
+  const unsigned long long z[8] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
   cudaMemcpyToSymbol(g_vq_tier_calls, z, sizeof z);
 }
 #endif

@@ -312,49 +312,56 @@ __global__ void __launch_bounds__(128) k_poly(Work w) {
     // diagonal candidates (else from the chains' extent).  Per box, s is the
     // largest tried value whose four corners pass the certain inside test.
     if (ok) {
-      double cx, cy, hx, hy;
+      // FP32 throughout (GB300's FP64 pipe is slow and the box is only a
+      // heuristic): each tested corner is an FP32 value, widened exactly, so
+      // the stored box is the one whose corners passed the test
+      float cx, cy, hx, hy;
       const int i1 = S.idx[4], i2 = S.idx[12], i3 = S.idx[20], i4 = S.idx[28];
-      const double x0 = fmax(S.x[12], S.x[20]), x1 = fmin(S.x[4], S.x[28]);
-      const double y0 = fmax(S.y[20], S.y[28]), y1 = fmin(S.y[4], S.y[12]);
+      const float x0 = fmaxf(S.fx[12], S.fx[20]), x1 = fminf(S.fx[4], S.fx[28]);
+      const float y0 = fmaxf(S.fy[20], S.fy[28]), y1 = fminf(S.fy[4], S.fy[12]);
       if (i1 >= 0 && i2 >= 0 && i3 >= 0 && i4 >= 0 && x0 < x1 && y0 < y1) {
-        cx = 0.5 * (x0 + x1); cy = 0.5 * (y0 + y1);
-        hx = 0.5 * (x1 - x0); hy = 0.5 * (y1 - y0);
+        cx = 0.5f * (x0 + x1); cy = 0.5f * (y0 + y1);
+        hx = 0.5f * (x1 - x0); hy = 0.5f * (y1 - y0);
       } else {
-        double sx = 0.0, sy = 0.0, ylo = S.y[lmin], yhi = S.y[lmin];
+        float sx = 0.0f, sy = 0.0f, ylo = S.fy[lmin], yhi = S.fy[lmin];
         const int nv = S.nu + S.nl;
-        for (int i = 0; i < S.nu; i++) { sx += S.x[S.cu[i]]; sy += S.y[S.cu[i]]; ylo = fmin(ylo, S.y[S.cu[i]]); yhi = fmax(yhi, S.y[S.cu[i]]); }
-        for (int i = 0; i < S.nl; i++) { sx += S.x[S.cl[i]]; sy += S.y[S.cl[i]]; ylo = fmin(ylo, S.y[S.cl[i]]); yhi = fmax(yhi, S.y[S.cl[i]]); }
-        cx = sx / nv; cy = sy / nv;
-        hx = 0.25 * (S.x[lmax] - S.x[lmin]); hy = 0.25 * (yhi - ylo);
+        for (int i = 0; i < S.nu; i++) { sx += S.fx[S.cu[i]]; sy += S.fy[S.cu[i]]; ylo = fminf(ylo, S.fy[S.cu[i]]); yhi = fmaxf(yhi, S.fy[S.cu[i]]); }
+        for (int i = 0; i < S.nl; i++) { sx += S.fx[S.cl[i]]; sy += S.fy[S.cl[i]]; ylo = fminf(ylo, S.fy[S.cl[i]]); yhi = fmaxf(yhi, S.fy[S.cl[i]]); }
+        cx = sx / (float)nv; cy = sy / (float)nv;
+        hx = 0.25f * (S.fx[lmax] - S.fx[lmin]); hy = 0.25f * (yhi - ylo);
       }
       // lane 8 b + j tries scale j of box b (its four corners in turn): a
       // coarse round over (0, 1], then a fine round between the largest
       // passing scale and the next coarser one
       const int b = lane >> 3, j = lane & 7;
-      const double fx = b == 1 ? 1.3066 : (b == 2 ? 0.5412 : 1.0), fy = b == 1 ? 0.5412 : (b == 2 ? 1.3066 : 1.0);
-      const double coarse[8] = {1.0, 0.97, 0.9, 0.8, 0.65, 0.5, 0.3, 0.1};
-      double best = 0.0;
+      const float fx = b == 1 ? 1.3066f : (b == 2 ? 0.5412f : 1.0f), fy = b == 1 ? 0.5412f : (b == 2 ? 1.3066f : 1.0f);
+      const float coarse[8] = {1.0f, 0.97f, 0.9f, 0.8f, 0.65f, 0.5f, 0.3f, 0.1f};
+      float best = 0.0f;
       for (int round = 0; round < 2; round++) {
-        double sc = coarse[j];
+        float sc = coarse[j];
         if (round == 1) {
-          const double hi = best == 1.0 ? 1.0 : (best > 0.0 ? best + (best >= 0.97 ? 0.03 : (best >= 0.9 ? 0.07 : 0.15)) : 0.1);
-          const double lo = best > 0.0 ? best : 0.0;
-          sc = lo + (hi - lo) * (double)(8 - j) / 8.0;
+          const float hi = best == 1.0f ? 1.0f : (best > 0.0f ? best + (best >= 0.97f ? 0.03f : (best >= 0.9f ? 0.07f : 0.15f)) : 0.1f);
+          const float lo = best > 0.0f ? best : 0.0f;
+          sc = lo + (hi - lo) * (float)(8 - j) * 0.125f;
         }
-        const double ex = sc * fx * hx, ey = sc * fy * hy;
-        bool in = b < kPolyBoxes && ex > 0.0 && ey > 0.0;
+        // explicit roundings (never contracted): the store below recomputes
+        // the same corners
+        const float ex = __fmul_rn(__fmul_rn(sc, fx), hx), ey = __fmul_rn(__fmul_rn(sc, fy), hy);
+        bool in = b < kPolyBoxes && ex > 0.0f && ey > 0.0f && isfinite(__fadd_rn(cx, ex)) && isfinite(__fadd_rn(cy, ey));
 #pragma unroll 1
-        for (int k = 0; k < 4 && in; k++) in = poly_inside(P, (k & 1) ? cx + ex : cx - ex, (k & 2) ? cy + ey : cy - ey);
+        for (int k = 0; k < 4 && in; k++)
+          in = poly_inside(P, f2d_exact((k & 1) ? __fadd_rn(cx, ex) : __fsub_rn(cx, ex)),
+                           f2d_exact((k & 2) ? __fadd_rn(cy, ey) : __fsub_rn(cy, ey)));
         // the largest passing scale of this box (lanes 8 b .. 8 b + 7)
-        double cand = in ? sc : 0.0;
+        float cand = in ? sc : 0.0f;
 #pragma unroll
-        for (int m = 4; m >= 1; m >>= 1) cand = fmax(cand, __shfl_xor_sync(kFull, cand, m));
-        best = fmax(best, cand);
+        for (int m = 4; m >= 1; m >>= 1) cand = fmaxf(cand, __shfl_xor_sync(kFull, cand, m));
+        best = fmaxf(best, cand);
       }
-      if (b < kPolyBoxes && j == 0 && best > 0.0) {
-        const double ex = best * fx * hx, ey = best * fy * hy;
-        P.box[b][0] = hword(cx - ex); P.box[b][1] = hword(cx + ex);
-        P.box[b][2] = hword(cy - ey); P.box[b][3] = hword(cy + ey);
+      if (b < kPolyBoxes && j == 0 && best > 0.0f) {
+        const float ex = __fmul_rn(__fmul_rn(best, fx), hx), ey = __fmul_rn(__fmul_rn(best, fy), hy);
+        P.box[b][0] = hword(f2d_exact(__fsub_rn(cx, ex))); P.box[b][1] = hword(f2d_exact(__fadd_rn(cx, ex)));
+        P.box[b][2] = hword(f2d_exact(__fsub_rn(cy, ey))); P.box[b][3] = hword(f2d_exact(__fadd_rn(cy, ey)));
       }
     }
     __syncwarp();

@@ -158,7 +158,7 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
           CandT<double> c;
           c.x = M.X[u]; c.y = M.Y[u]; c.idx = M.I[u];
           k3_key<FAST>(M, cur, f, c.x, c.y, c.lo, c.hi);
-          if (cand_beats(L, c, best)) { best = c; bslot = u; }
+          if (FAST ? cand_beats(M.lab[cur][f], L, c, best) : cand_beats(L, c, best)) { best = c; bslot = u; }
         }
         M.fr[f] = (short)bslot;
       }
@@ -172,10 +172,10 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
           CandT<double> c;
           c.x = M.X[u]; c.y = M.Y[u]; c.idx = M.I[u];
           k3_key<FAST>(M, cur, f, c.x, c.y, c.lo, c.hi);
-          if (cand_beats(L, c, best)) best = c;
+          if (FAST ? cand_beats(M.lab[cur][f], L, c, best) : cand_beats(L, c, best)) best = c;
         }
         const unsigned lanes = __ballot_sync(kFull, best.idx >= 0);
-        if (__popc(lanes) > 1) best = warp_best(L, best);
+        if (__popc(lanes) > 1) best = FAST ? warp_best(M.lab[cur][f], L, best) : warp_best(L, best);
         else if (lanes) best = shfl_xor_cand(best, lane ^ (__ffs(lanes) - 1));
         if (lane == 0) {
           // the winner's slot: the candidate with that index

@@ -252,14 +252,16 @@ __device__ void wl_finish(const Work& w, WlSmem& S, int sid) {
     const int n = ch ? nR : nL;
     if (n > 0) {
       const double* E = ch ? &G.rx : &G.ax;
+      const bool fast = (R.flags & kSegFast) != 0;
+      const LineF Lf = fast ? (ch ? line2_of(G) : line1_of(G)) : LineF{};
       CandT<double> b = cand_none<double>();
       for (int i = lane; i < nt; i += kWarp) {
         const BestRec r = load_rec(&w.wlrec[2 * (long long)(t0 + i) + ch]);
         if (r.idx < 0) continue;
         const CandT<double> c = from_rec(r);
-        if (cand_beats(E, c, b)) b = c;
+        if (fast ? cand_beats(Lf, E, c, b) : cand_beats(E, c, b)) b = c;
       }
-      b = warp_best(E, b);
+      b = fast ? warp_best(Lf, E, b) : warp_best(E, b);
       const int dst = wl_dst(R.flags);
       if (ch == 0) wl_child(w, R, R.a, R.r, b.idx, R.off, nL, dst, lane);
       else wl_child(w, R, R.r, R.b, b.idx, R.off + R.len - nR, nR, dst, lane);
@@ -368,10 +370,14 @@ __device__ void wl_tile(const Work& w, WlSmem& S, const WlTask& T, int h) {
       if (!((mc >> k) & 1u) || key_hi(key[k], err[k]) < Lc) continue;
       K kk, ee;
       line_key_tight(lc, E, X[k], Y[k], kk, ee);
-      take_best(b, E, X[k], Y[k], I[k], kk, ee);
+      if constexpr (FAST) take_best(b, lc, E, X[k], Y[k], I[k], kk, ee);
+      else take_best(b, E, X[k], Y[k], I[k], kk, ee);
     }
     const unsigned lanes = __ballot_sync(kFull, b.idx >= 0);
-    if (__popc(lanes) > 1) b = warp_best(E, b);  // usually one lane holds the only candidate
+    if (__popc(lanes) > 1) {  // usually one lane holds the only candidate
+      if constexpr (FAST) b = warp_best(lc, E, b);
+      else b = warp_best(E, b);
+    }
     else if (lanes) b = shfl_xor_cand(b, lane ^ (__ffs(lanes) - 1));
     const int n = __reduce_add_sync(kFull, __popc(mc));
     if (lane == 0) {
@@ -396,7 +402,10 @@ __device__ void wl_tile(const Work& w, WlSmem& S, const WlTask& T, int h) {
     }
     if (b.idx >= 0 && dkey(b.hi) < lo) b.idx = -1;
     const unsigned lanes = __ballot_sync(kFull, b.idx >= 0);
-    if (__popc(lanes) > 1) b = warp_best(E, b);
+    if (__popc(lanes) > 1) {
+      if constexpr (FAST) b = warp_best(ch ? l2 : l1, E, b);
+      else b = warp_best(E, b);
+    }
     else if (lanes) b = shfl_xor_cand(b, lane ^ (__ffs(lanes) - 1));
     if (lane == 0) w.wlrec[2 * (long long)h + ch] = to_rec(b);
 #ifdef VQ_WL_PROFILE
@@ -554,6 +563,9 @@ __global__ void __launch_bounds__(kWlThreads, 2) k_wl(const Work* __restrict__ w
 #endif
   for (;;) {
     WL_NOW(tp0);
+#ifdef VQ_WL_PROFILE
+    const unsigned long long cc0 = clock64();
+#endif
     if (threadIdx.x == 0) S.h = wl_pop(w, &S.task);
     __syncthreads();
     const int h = S.h;
@@ -609,7 +621,7 @@ __global__ void __launch_bounds__(kWlThreads, 2) k_wl(const Work* __restrict__ w
         e[4] = (unsigned long long)(long long)T.seg;
         e[5] = ((unsigned long long)(small ? T.R.level : S.u.t.seg.R.level) << 32) | (unsigned)(small ? T.R.len : T.count);
         e[6] = small ? 0ull : (unsigned long long)S.u.t.last;
-        e[7] = 0ull;
+        e[7] = clock64() - cc0;  // SM cycles from the claim to the end
       }
     }
 #endif

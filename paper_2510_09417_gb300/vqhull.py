@@ -90,6 +90,7 @@ class ServerInfo(ctypes.Structure):
 SYMBOLS = (
     "vq_status_string", "vq_version", "vq_hull2d", "vq_hull2d_aos", "vq_hull2d_batched", "vq_hull2d_host", "vq_hull2d_noalloc",
     "vq_get_config", "vq_set_config", "vq_last_stats", "vq_profile_read", "vq_autotune", "vq_debug_orient_f32",
+    "vq_debug_round_f32",
     "vq_server_create", "vq_server_submit",
     "vq_server_poll", "vq_server_wait", "vq_server_wait_any", "vq_server_stats", "vq_server_info_read", "vq_server_destroy",
 )
@@ -138,6 +139,8 @@ def load(build_if_missing: bool = True):
         lib.vq_autotune.restype = ctypes.c_int
         lib.vq_debug_orient_f32.argtypes = [vp, i64, i32, vp, vp, vp]
         lib.vq_debug_orient_f32.restype = ctypes.c_int
+        lib.vq_debug_round_f32.argtypes = [vp, i64, vp, vp]
+        lib.vq_debug_round_f32.restype = ctypes.c_int
         lib.vq_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
         lib.vq_server_create.restype = ctypes.c_int
         lib.vq_server_submit.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
@@ -298,6 +301,18 @@ def vq_set_config(cfg: Config | None = None, **kw) -> Config:
         setattr(c, k, v)
     _check(load().vq_set_config(ctypes.byref(c)), "vq_set_config")
     return c
+
+
+def vq_debug_round_f32(v: torch.Tensor, stream=None) -> torch.Tensor:
+    """The FP32 tiers' FP64 -> FP32 rounding (round to nearest, ties to even)
+    of device FP64 values: returns the FP32 results on the device."""
+    lib = load()
+    if not isinstance(v, torch.Tensor) or v.device.type != "cuda" or v.dtype != torch.float64:
+        raise TypeError("v must be a CUDA float64 tensor")
+    t = v.contiguous().reshape(-1)
+    out = torch.empty(t.shape[0], dtype=torch.float32, device=t.device)
+    _check(lib.vq_debug_round_f32(t.data_ptr(), t.shape[0], out.data_ptr(), _stream_ptr(stream)), "vq_debug_round_f32")
+    return out
 
 
 def vq_debug_orient_f32(tri: torch.Tensor, tier: int = 0, stream=None):

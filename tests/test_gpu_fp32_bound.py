@@ -108,3 +108,35 @@ def _arc_rows(rng_seed, m):
     rng = np.random.default_rng(rng_seed)
     rng.integers(-60, 40, m)
     return rng.integers(0, 6, m) == 4
+
+
+def test_round_f32_is_ieee_nearest_even(vq):
+    """The FP32 tiers round FP64 differences to FP32 with integer operations;
+    the result must be IEEE 754 round-to-nearest-even, bit for bit (numpy's
+    float64 -> float32 cast is that rounding): normal values, exact ties at
+    the 29 dropped bits, values at and across the subnormal boundary, FP32
+    overflow, signed zeros, infinities and NaNs."""
+    rng = np.random.default_rng(77)
+    m = 1 << 20
+    e = rng.integers(-160, 130, m)
+    v = np.ldexp(rng.random(m) + 0.5, e) * np.where(rng.random(m) < 0.5, -1.0, 1.0)
+    # ties and near-ties: FP32 values plus exactly half an FP32 ulp (+- 1 FP64 ulp)
+    f = rng.standard_normal(m // 4).astype(np.float32)
+    up = np.nextafter(f, np.float32(np.inf)).astype(np.float64)
+    half = (f.astype(np.float64) + up) / 2
+    ties = np.concatenate([half, np.nextafter(half, np.inf), np.nextafter(half, -np.inf)])
+    # the subnormal range and its boundary, and rounding that carries
+    sub = np.ldexp(rng.random(m // 4), rng.integers(-152, -124, m // 4))
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 3.4028234663852886e38, 3.4028235677973366e38,
+                        3.4028235677973362e38, -3.4028236e38, 2.0 ** -149, 2.0 ** -150, 2.0 ** -150 * 1.0000001,
+                        2.0 ** -126, 2.0 ** -126 * (1 - 2.0 ** -25), 1.0 - 2.0 ** -25, 1.0 + 2.0 ** -24,
+                        1.0 + 3 * 2.0 ** -24, 5e-324, -5e-324, 2.0 ** -1022])
+    x = np.concatenate([v, ties, sub, -sub, special])
+    got = vq.vq_debug_round_f32(torch.from_numpy(x).cuda()).cpu().numpy()
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float32)
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan)
+    gb, wb = got.view(np.uint32)[~nan], want.view(np.uint32)[~nan]
+    bad = np.flatnonzero(gb != wb)
+    assert bad.size == 0, (x[~nan][bad[:5]], gb[bad[:5]], wb[bad[:5]])
