@@ -725,7 +725,7 @@ __device__ __forceinline__ LineF line2_of(const SegGeom& g) {
 constexpr int kPolyDirs = 32;    // sampled directions (integer pairs, see k_sample)
 constexpr int kChainEdges = 16;  // at most 16 edges (15 inner vertices) per chain
 
-constexpr int kPolyBoxes = 3;    // inner boxes per set (aspect ratios 1, wide, tall)
+constexpr int kPolyBoxes = 5;    // inner boxes per set (corners at 45, 22.5, 67.5, 33.75, 56.25 degrees)
 
 struct alignas(16) PolyF {
   float box[kPolyBoxes][4];  // inner boxes: hword of x0, x1, y0, y1; empty: x0 = +inf
@@ -747,11 +747,12 @@ struct alignas(16) PolyF {
 // infinity (the implication still holds) or a NaN (every compare fails).
 __device__ __forceinline__ float hword(double v) { return __int_as_float(__double2hiint(v)); }
 
-// The point is certainly strictly inside one of the inner boxes.
-__device__ __forceinline__ bool in_boxes(const float (&b)[kPolyBoxes][4], float hx, float hy) {
+// The point is certainly strictly inside one of the inner boxes b[0 .. NB).
+template <int NB>
+__device__ __forceinline__ bool in_boxes(const float (&b)[NB][4], float hx, float hy) {
   bool in = false;
 #pragma unroll
-  for (int k = 0; k < kPolyBoxes; k++) in = in || (hx > b[k][0] && hx < b[k][1] && hy > b[k][2] && hy < b[k][3]);
+  for (int k = 0; k < NB; k++) in = in || (hx > b[k][0] && hx < b[k][1] && hy > b[k][2] && hy < b[k][3]);
   return in;
 }
 

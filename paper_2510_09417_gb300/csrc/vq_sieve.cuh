@@ -147,8 +147,21 @@ struct PolyScratch {
   int idx[kPolyDirs];                  // candidate point (global index) or -1
   int cu[kChainEdges + 1], cl[kChainEdges + 1];  // chain vertices as candidate slots, L first, R last
   int nu, nl;
+  float bb[kPolyBoxes];  // inner-box search: largest passing scale per box
   PolyF P;
 };
+
+// Inner boxes: box b has half sizes s (kBoxFx[b] hx, kBoxFy[b] hy) around
+// the centre, i.e. corners at angle t_b from the axes on an ellipse of
+// half axes sqrt(2) (hx, hy): t_b = 45, 22.5, 67.5, 33.75, 56.25 degrees,
+// (sqrt(2) cos t_b, sqrt(2) sin t_b).  On a disk the union of the five
+// covers about 90 % of the area (the first three 85 %, the first one 64 %).
+__device__ __forceinline__ float box_fx(int b) {
+  return b == 0 ? 1.0f : (b == 1 ? 1.3066f : (b == 2 ? 0.5412f : (b == 3 ? 1.1759f : 0.7857f)));
+}
+__device__ __forceinline__ float box_fy(int b) {
+  return b == 0 ? 1.0f : (b == 1 ? 0.5412f : (b == 2 ? 1.3066f : (b == 3 ? 0.7857f : 1.1759f)));
+}
 
 // Approximate orientation of three candidates (FP32 on truncated
 // coordinates): only used to choose chain vertices, which needs no
@@ -330,36 +343,45 @@ __global__ void __launch_bounds__(128) k_poly(Work w) {
         cx = sx / (float)nv; cy = sy / (float)nv;
         hx = 0.25f * (S.fx[lmax] - S.fx[lmin]); hy = 0.25f * (yhi - ylo);
       }
-      // lane 8 b + j tries scale j of box b (its four corners in turn): a
-      // coarse round over (0, 1], then a fine round between the largest
-      // passing scale and the next coarser one
-      const int b = lane >> 3, j = lane & 7;
-      const float fx = b == 1 ? 1.3066f : (b == 2 ? 0.5412f : 1.0f), fy = b == 1 ? 0.5412f : (b == 2 ? 1.3066f : 1.0f);
-      const float coarse[8] = {1.0f, 0.97f, 0.9f, 0.8f, 0.65f, 0.5f, 0.3f, 0.1f};
-      float best = 0.0f;
-      for (int round = 0; round < 2; round++) {
+      // lane 6 b + j (j < 6, b < kPolyBoxes) tests scale j of box b (its
+      // four corners in turn): a coarse round over (0, 1], then two rounds
+      // that split the gap above the largest passing scale into 7 parts;
+      // per box the largest passing scale is kept with an atomic maximum on
+      // its bits (non-negative floats order as their bit patterns)
+      constexpr int kScales = 6;
+      static_assert(kScales * kPolyBoxes <= kWarp, "one try per lane");
+      const float coarse[kScales] = {1.0f, 0.95f, 0.85f, 0.7f, 0.5f, 0.25f};
+      if (lane < kPolyBoxes) S.bb[lane] = 0.0f;
+      __syncwarp();
+      const int b = lane / kScales, j = lane - b * kScales;
+      const bool box = b < kPolyBoxes;
+      const float fx = box ? box_fx(b) : 0.0f, fy = box ? box_fy(b) : 0.0f;
+      float gap = 0.0f;  // width of the interval the next round splits
+      for (int round = 0; round < 3; round++) {
+        const float best = box ? S.bb[b] : 0.0f;
         float sc = coarse[j];
-        if (round == 1) {
-          const float hi = best == 1.0f ? 1.0f : (best > 0.0f ? best + (best >= 0.97f ? 0.03f : (best >= 0.9f ? 0.07f : 0.15f)) : 0.1f);
-          const float lo = best > 0.0f ? best : 0.0f;
-          sc = lo + (hi - lo) * (float)(8 - j) * 0.125f;
+        if (round == 1) {  // the gap up to the next coarse scale
+          gap = best >= 1.0f ? 0.0f : (best >= 0.95f ? 0.05f : (best >= 0.85f ? 0.1f : (best >= 0.7f ? 0.15f : (best >= 0.5f ? 0.2f : (best >= 0.25f ? 0.25f : 0.25f)))));
+        } else if (round == 2) {
+          gap = gap * (1.0f / 7.0f);
         }
+        if (round > 0) sc = best + gap * (float)(kScales - j) * (1.0f / 7.0f);
         // explicit roundings (never contracted): the store below recomputes
         // the same corners
         const float ex = __fmul_rn(__fmul_rn(sc, fx), hx), ey = __fmul_rn(__fmul_rn(sc, fy), hy);
-        bool in = b < kPolyBoxes && ex > 0.0f && ey > 0.0f && isfinite(__fadd_rn(cx, ex)) && isfinite(__fadd_rn(cy, ey));
+        bool in = box && sc > best && ex > 0.0f && ey > 0.0f && isfinite(__fadd_rn(cx, ex)) && isfinite(__fadd_rn(cy, ey));
 #pragma unroll 1
         for (int k = 0; k < 4 && in; k++)
           in = poly_inside(P, f2d_exact((k & 1) ? __fadd_rn(cx, ex) : __fsub_rn(cx, ex)),
                            f2d_exact((k & 2) ? __fadd_rn(cy, ey) : __fsub_rn(cy, ey)));
-        // the largest passing scale of this box (lanes 8 b .. 8 b + 7)
-        float cand = in ? sc : 0.0f;
-#pragma unroll
-        for (int m = 4; m >= 1; m >>= 1) cand = fmaxf(cand, __shfl_xor_sync(kFull, cand, m));
-        best = fmaxf(best, cand);
+        __syncwarp();
+        if (in) atomicMax(reinterpret_cast<int*>(&S.bb[b]), __float_as_int(sc));
+        __syncwarp();
       }
-      if (b < kPolyBoxes && j == 0 && best > 0.0f) {
-        const float ex = __fmul_rn(__fmul_rn(best, fx), hx), ey = __fmul_rn(__fmul_rn(best, fy), hy);
+      if (lane < kPolyBoxes && S.bb[lane] > 0.0f) {
+        const int b = lane;
+        const float best = S.bb[b];
+        const float ex = __fmul_rn(__fmul_rn(best, box_fx(b)), hx), ey = __fmul_rn(__fmul_rn(best, box_fy(b)), hy);
         P.box[b][0] = hword(f2d_exact(__fsub_rn(cx, ex))); P.box[b][1] = hword(f2d_exact(__fadd_rn(cx, ex)));
         P.box[b][2] = hword(f2d_exact(__fsub_rn(cy, ey))); P.box[b][3] = hword(f2d_exact(__fadd_rn(cy, ey)));
       }
@@ -422,9 +444,12 @@ __global__ void __launch_bounds__(32 * kSvWarps, 3) k_sieve(Work w) {
   int set_end = w.k0_tile_start[set + 1];
   SetRec S = w.sets[set];
   const PolyF* P = w.poly + set;
-  float bx[kPolyBoxes][4];
+  // the first three inner boxes in registers (the test of every point);
+  // the others are read on the compacted rest
+  constexpr int kRegBoxes = 3;
+  float bx[kRegBoxes][4];
 #pragma unroll
-  for (int b = 0; b < kPolyBoxes; b++)
+  for (int b = 0; b < kRegBoxes; b++)
 #pragma unroll
     for (int c = 0; c < 4; c++) bx[b][c] = P->box[b][c];
   int on = P->on;
@@ -485,6 +510,38 @@ __global__ void __launch_bounds__(32 * kSvWarps, 3) k_sieve(Work w) {
         n += __popc(b);
       }
       __syncwarp();
+      // the other boxes on full warps; what they leave is compacted again
+      // in place (a lane writes at or below the position every lane read)
+      if (kPolyBoxes > kRegBoxes && n > kWarp) {  // they can save a chain-test pass
+        float xb[kPolyBoxes - kRegBoxes][4];
+#pragma unroll
+        for (int b = 0; b < kPolyBoxes - kRegBoxes; b++)
+#pragma unroll
+          for (int c = 0; c < 4; c++) xb[b][c] = P->box[kRegBoxes + b][c];
+        int n2 = 0;
+        for (int i0 = 0; i0 < n; i0 += kWarp) {
+          const int i = i0 + lane;
+          bool o = false;
+          double ux = 0.0, uy = 0.0;
+          int ui = 0;
+          if (i < n) {
+            ux = R.x[i];
+            uy = R.y[i];
+            ui = R.i[i];
+            o = !in_boxes(xb, hword(ux), hword(uy));
+          }
+          const unsigned b = __ballot_sync(kFull, o);
+          if (o) {
+            const int d = n2 + __popc(b & lt);
+            R.x[d] = ux;
+            R.y[d] = uy;
+            R.i[d] = ui;
+          }
+          n2 += __popc(b);
+        }
+        __syncwarp();
+        n = n2;
+      }
       // chain test on full warps; the points it cannot place inside are kept
       for (int i0 = 0; i0 < n; i0 += kWarp) {
         const int i = i0 + lane;
@@ -548,7 +605,7 @@ __global__ void __launch_bounds__(32 * kSvWarps, 3) k_sieve(Work w) {
       S = w.sets[set];
       P = w.poly + set;
 #pragma unroll
-      for (int b = 0; b < kPolyBoxes; b++)
+      for (int b = 0; b < kRegBoxes; b++)
 #pragma unroll
         for (int c = 0; c < 4; c++) bx[b][c] = P->box[b][c];
       on = P->on;
