@@ -26,6 +26,16 @@ __device__ __forceinline__ bool vq_check_idx(const Work& w, int site, long long 
 __device__ __forceinline__ double px(const Work& w, long long i) { return w.x[w.aos ? 2 * i : i]; }
 __device__ __forceinline__ double py(const Work& w, long long i) { return w.y[w.aos ? 2 * i : i]; }
 
+// Segments of at most this many points are finished in shared memory.  A
+// hull-dense set (flag kSegDense: the pre-filter kept more than half of its
+// points, so nearly every point is a hull vertex) uses the finisher's full
+// capacity: its recursion is as deep as the segment is long, which the
+// finisher's rounds take far faster than partition levels.  Only the
+// routing changes; the result and the per-level counters do not.
+__device__ __forceinline__ int seg_small_max(const Work& w, int flags) {
+  return (flags & kSegDense) ? (kK3Cap > w.small_max ? kK3Cap : w.small_max) : w.small_max;
+}
+
 __device__ __forceinline__ bool fatal(const Work& w) {
   return (*reinterpret_cast<volatile unsigned*>(&w.ctrl->err) & kErrFatal) != 0;
 }

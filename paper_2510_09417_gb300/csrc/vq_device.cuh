@@ -40,6 +40,8 @@ constexpr unsigned kErrFatal = kErrTimeout | kErrCapacity | kErrInternal | kErrB
 constexpr int kSegFast = 1;       // FP32 tier allowed (all |coords| < 2^40)
 constexpr int kSegSrcInput = 2;   // points still in the caller's arrays (level 0)
 constexpr int kSegSrcBuf1 = 4;    // points in ping-pong buffer 1 (else buffer 0)
+constexpr int kSegDense = 8;      // hull-dense set (most points kept by the pre-filter): segments of up to
+                                  // the finisher's capacity go to it (see seg_small_max)
 
 // look-back status words: 2 flag bits, 31-bit left count, 31-bit right count
 constexpr unsigned long long kStAgg = 1ull << 62;

@@ -497,7 +497,8 @@ __device__ void k0_finish_set(const Work& w, int s, SetRec S, const LexPt& mn, c
   R.tile_base = 0;
   R.ntiles = 0;
   R.flags = S.flags | (w.sieve ? kSegSrcBuf1 : kSegSrcInput);
-  if (R.len <= w.small_max) {
+  if (w.sieve && 2LL * R.len > (long long)S.len) R.flags |= kSegDense;
+  if (R.len <= seg_small_max(w, R.flags)) {
     if (lane == 0) push_k3(w, R);
   } else {
     push_k1_warp(w, 0, R, lane);
@@ -1044,8 +1045,8 @@ __device__ void make_child(const Work& w, const SegRec& P, int a, int b, int r, 
   C.level = level;
   C.tile_base = 0;
   C.ntiles = 0;
-  C.flags = (P.flags & kSegFast) | (buf ? kSegSrcBuf1 : 0);
-  if (len <= w.small_max) {
+  C.flags = (P.flags & (kSegFast | kSegDense)) | (buf ? kSegSrcBuf1 : 0);
+  if (len <= seg_small_max(w, C.flags)) {
     if (lane == 0) push_k3(w, C);
   } else {
     push_k1_warp(w, (level & 1), C, lane);

@@ -218,8 +218,8 @@ __device__ void wl_child(const Work& w, const SegRec& P, int a, int b, int r, in
   C.level = P.level + 1;
   C.tile_base = 0;
   C.ntiles = 0;
-  C.flags = (P.flags & kSegFast) | (buf ? kSegSrcBuf1 : 0);
-  if (len <= w.small_max) {
+  C.flags = (P.flags & (kSegFast | kSegDense)) | (buf ? kSegSrcBuf1 : 0);
+  if (len <= seg_small_max(w, C.flags)) {
     if (lane == 0) wl_push_small(w, C);
   } else {
     wl_push_big(w, C, lane);
