@@ -54,10 +54,10 @@ FULL_N = 100_000_000
 # sieve launch on 2e7-point square and disk hulls (profiles/): the input is
 # read once (16 B per point) and the kept points are written.  Traffic grows
 # in proportion to the points, so a launch's traffic is this times n.
-SIEVE_DRAM_BYTES_PER_POINT = 16.2
+SIEVE_DRAM_BYTES_PER_POINT = 16.08
 # DRAM bytes of every kernel of one hull per input point (ncu, all launches
 # of one 2e7-point hull; profiles/), per distribution.
-HULL_DRAM_BYTES_PER_POINT = {"square": 16.61, "disk": 17.47}
+HULL_DRAM_BYTES_PER_POINT = {"square": 16.25, "disk": 16.43}
 
 
 def bench_configs(vq, torch, stream, dev, survivors, peak, reps=5):
@@ -605,15 +605,18 @@ def main():
                 "timing": "CUDA events around every sieve launch, over a second pass of the same K steps "
                           f"({ms_prof / args.steps:.3f} ms per step with the events, "
                           f"{ms / args.steps:.3f} ms without)"}
-    # the partition kernel (all levels) against the same peak: 20 bytes per
-    # point read and per point kept
-    k1_bytes = 20.0 * (prof["k1_points_read"] + prof["k1_points_kept"])
-    k1_s = prof["k1_ms"] / 1e3
+    # the recursion after the sieve: the level loop hands its segments to the
+    # persistent worklist (at level 0 on these inputs), whose time is spent
+    # on the recursion's dependent chain of tasks, not on bytes (under 0.2 B
+    # per input point, profiles/bench_launch_list.md); the level-loop
+    # partition kernel runs only above the handover level
+    calls = max(prof["calls"], 1)
     roofline["other_kernels"] = {
-        "k_k1w (partition, all levels)": {
-            "achieved": k1_bytes / k1_s / 1e9 if k1_s > 0 else 0.0, "unit": "GB/s",
-            "frac": (k1_bytes / k1_s / 1e9) / peak if k1_s > 0 else 0.0,
-            "launches": int(prof["k1_launches"]), "ms_per_hull": prof["k1_ms"] / max(prof["calls"], 1)}}
+        "k_wl (persistent worklist, the recursion below the handover level)": {
+            "bound": "latency", "ms_per_hull": prof["k5_ms"] / calls,
+            "points_classified_per_hull": prof["k1_points_read"] / calls},
+        "k_k1w (level-loop partition, levels above the handover)": {
+            "launches": int(prof["k1_launches"]), "ms_per_hull": prof["k1_ms"] / calls}}
     # the whole hull: DRAM bytes per hull (ncu, all kernels) over the device
     # time per hull of the value's timed region
     hull_ms = ms_max / args.steps / 2
