@@ -717,7 +717,7 @@ size_t batched_workspace_bytes(long long N, int nsets) {
 
 vq_status batched_run(Ctx* c, void* workspace, size_t bytes, const double* x, const double* y,
                       const long long* offsets, int nsets, long long N, int* hull_idx, long long* hull_offsets,
-                      cudaStream_t st) {
+                      cudaStream_t st, long long* h_total) {
   if (!c || !workspace || !offsets || !hull_offsets || nsets < 1 || N < 0) return VQ_ERR_INVALID_ARG;
   if (N + nsets > (long long)INT_MAX - 2) return VQ_ERR_TOO_LARGE;
   if (N > 0 && (!x || !y || !hull_idx)) return VQ_ERR_INVALID_ARG;
@@ -725,7 +725,7 @@ vq_status batched_run(Ctx* c, void* workspace, size_t bytes, const double* x, co
   c->mem = static_cast<char*>(workspace);
   c->bytes = bytes;
   c->external = true;
-  const vq_status s = run(*c, x, y, offsets, 0, nsets, N, hull_idx, hull_offsets, nullptr, st);
+  const vq_status s = run(*c, x, y, offsets, 0, nsets, N, hull_idx, hull_offsets, h_total, st);
   c->mem = nullptr;
   c->bytes = 0;
   c->external = false;

@@ -151,6 +151,6 @@ size_t batched_workspace_bytes(long long N, int nsets);
 // (at least batched_workspace_bytes(N, nsets) bytes, 256-byte aligned)
 vq_status batched_run(Ctx* c, void* workspace, size_t bytes, const double* x, const double* y,
                       const long long* offsets, int nsets, long long N, int* hull_idx, long long* hull_offsets,
-                      cudaStream_t st);
+                      cudaStream_t st, long long* h_total = nullptr);
 
 }  // namespace vq

@@ -32,6 +32,10 @@ using Clock = std::chrono::steady_clock;
 constexpr int kDefaultLanes = 3;
 constexpr int kMaxLanes = 16;
 constexpr size_t kBytesFixed = 1 << 20;  // the budget must at least cover this
+// A batch is the queue's head and the requests after it while the batch
+// holds at most max(kBatchPoints, head's points) points: small requests share
+// level steps, and a big request does not hold small ones back behind it.
+constexpr long long kBatchPoints = 1ll << 20;
 constexpr size_t kDefaultPinned = 8ull << 30;  // pinned staging area (at most the budget)
 
 struct Request {
@@ -126,8 +130,20 @@ static int admit_count(const vq_server* s, int limit, long long* points, size_t*
   if (limit > 0) nq = std::min(nq, limit);
   std::vector<int64_t> sizes((size_t)nq);
   for (int i = 0; i < nq; i++) sizes[(size_t)i] = s->queue[(size_t)i]->n;
-  return vq::admit_prefix(sizes.data(), nq, s->resident, s->used, kBytesFixed, s->cfg.max_inflight,
-                          s->cfg.mem_budget_bytes, batch_bytes, points, bytes);
+  int k = vq::admit_prefix(sizes.data(), nq, s->resident, s->used, kBytesFixed, s->cfg.max_inflight,
+                           s->cfg.mem_budget_bytes, batch_bytes, points, bytes);
+  if (k > 1) {
+    const long long cap = std::max<long long>(kBatchPoints, sizes[0]);
+    long long pts = sizes[0];
+    int j = 1;
+    while (j < k && pts + sizes[(size_t)j] <= cap) pts += sizes[(size_t)j++];
+    if (j < k) {
+      k = j;
+      *points = pts;
+      *bytes = batch_bytes(pts, k);
+    }
+  }
+  return k;
 }
 
 // The queue's head can be admitted now (caller holds mu).
@@ -156,6 +172,7 @@ static vq_status run_batch(vq_server* s, Lane* L, const std::vector<Request*>& b
   std::vector<int64_t> offs(ns + 1, 0);
   for (int i = 0; i < ns; i++) offs[i + 1] = offs[i] + batch[i]->n;
   vq_status st = VQ_OK;
+  long long total = 0;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < ns && e == cudaSuccess; i++) {
     const Request* r = batch[i];
@@ -172,17 +189,16 @@ static vq_status run_batch(vq_server* s, Lane* L, const std::vector<Request*>& b
     st = VQ_ERR_CUDA;
   } else {
     st = vq::batched_run(L->ctx, mem + B.ws, B.ws_bytes, dx, dy, reinterpret_cast<const long long*>(doff), ns, N,
-                         dout, reinterpret_cast<long long*>(dhoff), L->st);
+                         dout, reinterpret_cast<long long*>(dhoff), L->st, &total);
   }
   if (st == VQ_OK || st == VQ_ERR_NONFINITE) {
+    // the run ended with a synchronisation and returned the total, so the
+    // offsets and the vertices come back in one round trip
     hoff.assign(ns + 1, 0);
+    out.resize((size_t)std::max<long long>(total, 1));
     e = cudaMemcpyAsync(hoff.data(), dhoff, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost, L->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(L->st);
-    if (e == cudaSuccess) {
-      out.resize((size_t)std::max<int64_t>(hoff[ns], 1));
-      if (hoff[ns] > 0)
-        e = cudaMemcpyAsync(out.data(), dout, sizeof(int32_t) * hoff[ns], cudaMemcpyDeviceToHost, L->st);
-    }
+    if (e == cudaSuccess && total > 0)
+      e = cudaMemcpyAsync(out.data(), dout, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, L->st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       st = VQ_ERR_CUDA;
