@@ -49,11 +49,12 @@ __device__ __forceinline__ void emit(const Work& w, long long key, int local) {
   w.slot[key] = local;
 }
 
-__device__ __forceinline__ void add_stats(const Work& w, int level, long long rd, long long kept) {
+__device__ __forceinline__ void add_stats(const Work& w, int level, long long rd, long long kept,
+                                          long long segs = 1) {
   const int l = level < kMaxLevels ? level : kMaxLevels - 1;
   atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[l]), (unsigned long long)rd);
   atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[kMaxLevels + l]), (unsigned long long)kept);
-  atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[2 * kMaxLevels + l]), 1ull);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&w.stats[2 * kMaxLevels + l]), (unsigned long long)segs);
 }
 
 __device__ __forceinline__ long long warp_sum_ll(long long v) {

@@ -200,16 +200,18 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
     for (int k = 0; k < kK3PPT; k++) M.FR[nxt][tid * kK3PPT + k] = kNoFrame;
     __syncthreads();
     // C. classify every point of every frame; move it to its child's range
-    int npos[kK3PPT], ncls[kK3PPT], nfr[kK3PPT];
+    int npos[kK3PPT], ncls[kK3PPT], nfr[kK3PPT], nu[kK3PPT];
 #pragma unroll
     for (int k = 0; k < kK3PPT; k++) {
       const int q = tid * kK3PPT + k;
       ncls[k] = 0;
       npos[k] = 0;
       nfr[k] = 0;
+      nu[k] = 0;
       const int f = M.FR[cur][q];
       if (f == kNoFrame) continue;
       const int u = M.P[cur][q];
+      nu[k] = u;
       const int a = M.fa[cur][f], b = M.fb[cur][f], r = M.fr[f];
       SegGeom G;
       G.ax = M.X[a]; G.ay = M.Y[a]; G.rx = M.X[r]; G.ry = M.Y[r]; G.bx = M.X[b]; G.by = M.Y[b];
@@ -219,9 +221,27 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
       if (c == 3) c = classify_exact(&G, M.X[u], M.Y[u]);
       ncls[k] = c;
       nfr[k] = f;
-      if (c == 1) npos[k] = M.lo[cur][f] + atomicAdd(&M.nl[f], 1);
-      if (c == 2) npos[k] = M.hi[cur][f] - 1 - atomicAdd(&M.nr[f], 1);
-      if (c != 0) M.P[nxt][npos[k]] = (unsigned short)u;
+    }
+    // positions in the children's ranges: the lanes of a warp that move a
+    // point into the same child share one shared-memory atomic (early
+    // rounds have a few large frames, whose cursors every point hits)
+    {
+      const int lane = tid & 31;
+      const unsigned lt = lanemask_lt();
+#pragma unroll
+      for (int k = 0; k < kK3PPT; k++) {
+        const int c = ncls[k], f = nfr[k];
+        const unsigned key = (c == 1 || c == 2) ? (((unsigned)f << 1) | (unsigned)(c - 1)) : 0xffffffffu;
+        const unsigned mm = __match_any_sync(kFull, key);
+        if (key != 0xffffffffu) {
+          const int leader = __ffs(mm) - 1;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(c == 1 ? &M.nl[f] : &M.nr[f], __popc(mm));
+          base = __shfl_sync(mm, base, leader) + __popc(mm & lt);
+          npos[k] = c == 1 ? M.lo[cur][f] + base : M.hi[cur][f] - 1 - base;
+          M.P[nxt][npos[k]] = (unsigned short)nu[k];
+        }
+      }
     }
     __syncthreads();
     // D. per frame (two per thread, in frame order): emit r and the
@@ -229,6 +249,7 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
     constexpr int FPT = (kK3Frames + kK3Threads - 1) / kK3Threads;
     int nchild[FPT];
     int mine = 0;
+    unsigned long long st_read = 0, st_kept = 0, st_segs = 0;  // this round's counters (one level)
 #pragma unroll
     for (int k = 0; k < FPT; k++) {
       const int f = tid * FPT + k;
@@ -236,19 +257,32 @@ __device__ void k3_solve(const Work& w, const SegRec& S, K3Smem& M, int len, int
       if (f >= F) continue;
       const int lo = M.lo[cur][f], hi = M.hi[cur][f], nl = M.nl[f], nr = M.nr[f], r = M.fr[f];
       emit(w, (long long)S.off + lo + nl + 1 + S.shift, M.I[r] - S.set_off);
-      const int lvl = S.level + depth;
-      if (lvl < kK3StatLevels) {
-        atomicAdd(&M.kst[0][lvl], (unsigned long long)(hi - lo));
-        atomicAdd(&M.kst[1][lvl], (unsigned long long)(nl + nr));
-        atomicAdd(&M.kst[2][lvl], 1ull);
-      } else {
-        add_stats(w, lvl, hi - lo, nl + nr);
-      }
+      st_read += (unsigned long long)(hi - lo);
+      st_kept += (unsigned long long)(nl + nr);
+      st_segs += 1ull;
       // a single point is its own farthest point: Alg. 1, |P| <= 1
       if (nl == 1) emit(w, (long long)S.off + lo + 1 + S.shift, M.I[M.P[nxt][lo]] - S.set_off);
       if (nr == 1) emit(w, (long long)S.off + hi + S.shift, M.I[M.P[nxt][hi - 1]] - S.set_off);
       nchild[k] = (nl >= 2 ? 1 : 0) + (nr >= 2 ? 1 : 0);
       mine += nchild[k];
+    }
+    {  // every frame of a round is at level S.level + depth: one add per warp
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) {
+        st_read += __shfl_xor_sync(kFull, st_read, m);
+        st_kept += __shfl_xor_sync(kFull, st_kept, m);
+        st_segs += __shfl_xor_sync(kFull, st_segs, m);
+      }
+      const int lvl = S.level + depth;
+      if ((tid & 31) == 0 && st_segs > 0) {
+        if (lvl < kK3StatLevels) {
+          atomicAdd(&M.kst[0][lvl], st_read);
+          atomicAdd(&M.kst[1][lvl], st_kept);
+          atomicAdd(&M.kst[2][lvl], st_segs);
+        } else {
+          add_stats(w, lvl, (long long)st_read, (long long)st_kept, (long long)st_segs);
+        }
+      }
     }
     int F2 = 0;
     int b0 = k3_scan(mine, M.wsum, &F2);
