@@ -35,6 +35,24 @@ inline int admit_prefix(const int64_t* sizes, int nqueued, long long resident, s
   return k;
 }
 
+// The batch a lane runs: of an admissible prefix of k requests, the head
+// and the requests after it while the batch holds at most max(cap_points,
+// the head's points) points, so that small requests share level steps and
+// a big request does not hold small ones back behind it.  Returns the
+// batch's length (1 <= result <= k when k >= 1) and its points.
+inline int batch_prefix(const int64_t* sizes, int k, long long cap_points, long long* batch_points) {
+  if (k <= 0) {
+    *batch_points = 0;
+    return 0;
+  }
+  const long long cap = cap_points > sizes[0] ? cap_points : (long long)sizes[0];
+  long long pts = sizes[0];
+  int j = 1;
+  while (j < k && pts + sizes[j] <= cap) pts += sizes[j++];
+  *batch_points = pts;
+  return j;
+}
+
 // Free extents of a staging area (offset -> bytes): first-fit takes, and
 // returns merged with their free neighbours.
 class Extents {

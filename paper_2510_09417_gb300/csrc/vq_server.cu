@@ -133,10 +133,8 @@ static int admit_count(const vq_server* s, int limit, long long* points, size_t*
   int k = vq::admit_prefix(sizes.data(), nq, s->resident, s->used, kBytesFixed, s->cfg.max_inflight,
                            s->cfg.mem_budget_bytes, batch_bytes, points, bytes);
   if (k > 1) {
-    const long long cap = std::max<long long>(kBatchPoints, sizes[0]);
-    long long pts = sizes[0];
-    int j = 1;
-    while (j < k && pts + sizes[(size_t)j] <= cap) pts += sizes[(size_t)j++];
+    long long pts = 0;
+    const int j = vq::batch_prefix(sizes.data(), k, kBatchPoints, &pts);
     if (j < k) {
       k = j;
       *points = pts;

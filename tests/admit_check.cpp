@@ -27,6 +27,20 @@ int main() {
   // with it, one byte less leaves room for the first only
   run("reserve_fits", q, 4, 0, 5000, 64, 5000 + 68 * 300 + 2000 + 4096, 4096);
   run("reserve_short", q, 4, 0, 5000, 64, 5000 + 68 * 300 + 2000 + 4095, 4096);
+  // a lane's batch: the head and what follows while the batch holds at most
+  // max(cap, head) points
+  {
+    const int64_t b[5] = {100, 200, 300, 5000, 50};
+    long long bp = -1;
+    int j = vq::batch_prefix(b, 5, 600, &bp);
+    std::printf("batch_cap %d %lld\n", j, bp);  // 100 + 200 + 300 = 600 fits, 5000 does not
+    j = vq::batch_prefix(b + 3, 2, 600, &bp);
+    std::printf("batch_big_head %d %lld\n", j, bp);  // 5000 alone (5050 > max(600, 5000))
+    j = vq::batch_prefix(b, 5, 1 << 20, &bp);
+    std::printf("batch_all %d %lld\n", j, bp);
+    j = vq::batch_prefix(b, 0, 600, &bp);
+    std::printf("batch_none %d %lld\n", j, bp);
+  }
   // pinned staging extents: first fit, merging on return
   vq::Extents e;
   e.give(0, 1000);

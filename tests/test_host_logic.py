@@ -193,6 +193,12 @@ def test_server_admission_policy(tmp_path):
     assert got["empty"] == (0, 0, 0)
     assert got["reserve_fits"] == (2, 300, 68 * 300 + 2000)
     assert got["reserve_short"] == (1, 100, 68 * 100 + 1000)
+    # a lane's batch stops before the request that would take it past
+    # max(cap, head's points); a big head runs alone
+    assert got["batch_cap"] == (3, 600)
+    assert got["batch_big_head"] == (1, 5000)
+    assert got["batch_all"] == (5, 5650)
+    assert got["batch_none"] == (0, 0)
     # pinned staging extents: three of 300 fit in 1000 (first fit: 0, 300,
     # 600), a fourth does not; a freed hole of 300 cannot hold 301; returning
     # everything merges into one extent of 1000
